@@ -1,0 +1,251 @@
+"""Pins of the oracle's field side against closed forms fixed by the paper and
+by vector calculus (none of them re-types the oracle's own formulas):
+
+* flux functions of Eq. 37 (dipole) and Eq. 32 (monopole) recovered by the
+  theta-prefix of Eq. 27 at every node;
+* the face-averaged B of an exactly known field (uniform B_z) and the
+  second-order convergence of B to the point dipole;
+* div B = 0 preserved by Faraday's law (Eq. 18);
+* Michel's monopole (Eqs. 32-35): force-free perpendicular current,
+  stationarity under one force-free step, the corotation boundary value,
+  E.B = 0 and E^2 <= B^2 after the renormalisation of Eqs. 25-26, and the
+  spin-down power L_M;
+* the blending function of Eqs. 29-31 with the Table 1 bands.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2406_14512_gb300 import workloads
+
+
+def mk(nr, nt, geom, r_max=30.0, r_lc=3.0, **kw):
+    c = dict(nr=nr, nt=nt, r_min=1.0, r_max=r_max, r_lc=r_lc, b_star=1.0, geom=geom,
+             courant=0.5, r_abs=kw.pop("r_abs", 0.9 * r_max), absorb_strength=0.1,
+             psi_break=[], f_break=[], q=[-1.0, 1.0], m=[1.0, 1.0], inject=False,
+             capacity=0, seed=1)
+    c.update(kw)
+    return c
+
+
+def grid(o):
+    nr, nt = o.nr, o.nt
+    d = math.log(o.cfg["r_max"] / o.cfg["r_min"]) / nr
+    rn = o.cfg["r_min"] * np.exp(np.arange(nr + 1) * d)
+    rh = o.cfg["r_min"] * np.exp((np.arange(nr) + 0.5) * d)
+    tn = np.arange(nt + 1) * math.pi / nt
+    th = (np.arange(nt) + 0.5) * math.pi / nt
+    return rn, rh, tn, th
+
+
+def test_psi_dipole_and_monopole_exact_at_nodes(oracle_mod):
+    for geom, closed in [("dipole", lambda r, t: np.sin(t) ** 2 / r),
+                         ("monopole", lambda r, t: 1.0 - np.cos(t))]:
+        o = oracle_mod.Oracle(mk(40, 36, geom))
+        o.step(1, oracle_mod.ST["node"])
+        rn, _, tn, _ = grid(o)
+        ref = closed(rn[:, None], tn[None, :])
+        psi = o.get("psi")
+        assert np.max(np.abs(psi - ref)) < 1e-13 * np.max(np.abs(ref)), geom
+
+
+def test_uniform_field_face_averages_exact(oracle_mod):
+    """B = B0 z: the exact average of B_r = B0 cos(theta) over the zone
+    [theta_j, theta_j+1] is B0 (cos theta_j + cos theta_j+1)/2, and
+    B_theta = -B0 sin(theta) exactly."""
+    o = oracle_mod.Oracle(mk(24, 20, "uniform", r_max=10.0))
+    rn, rh, tn, th = grid(o)
+    br = o.get("B_r")
+    assert np.allclose(br, 0.5 * (np.cos(tn[:-1]) + np.cos(tn[1:]))[None, :], rtol=0, atol=1e-13)
+    bt = o.get("B_th")
+    ref = -np.sin(tn)[None, :] * np.ones((o.nr, 1))
+    ref[:, 0] = ref[:, -1] = 0.0
+    assert np.allclose(bt, ref, rtol=0, atol=1e-12)
+    assert np.all(o.get("B_ph") == 0)
+
+
+def test_dipole_field_converges_second_order(oracle_mod):
+    errs = []
+    for n in (32, 64, 128):
+        o = oracle_mod.Oracle(mk(n, n, "dipole", r_max=10.0))
+        rn, rh, tn, th = grid(o)
+        br = o.get("B_r")
+        ref = 2.0 * np.cos(th)[None, :] / rn[:, None] ** 3
+        errs.append(np.max(np.abs(br - ref) * rn[:, None] ** 3))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.8, (errs, rates)
+
+
+def div_b(o, r_below=np.inf):
+    """Net magnetic flux out of every cell (Gauss's theorem over the exact
+    faces) relative to the largest face flux, for cells below r_below."""
+    rn, rh, tn, th = grid(o)
+    br, bt = o.get("B_r"), o.get("B_th")
+    ar = 2 * math.pi * rn[:, None] ** 2 * (np.cos(tn[:-1]) - np.cos(tn[1:]))[None, :]
+    at = math.pi * np.sin(tn)[None, :] * (rn[1:] ** 2 - rn[:-1] ** 2)[:, None]
+    flux = br[1:] * ar[1:] - br[:-1] * ar[:-1] + bt[:, 1:] * at[:, 1:] - bt[:, :-1] * at[:, :-1]
+    rows = rn[1:] < r_below
+    return np.max(np.abs(flux[rows])) / np.max(np.abs(br[:-1] * ar[:-1]))
+
+
+def test_div_b_zero_preserved(oracle_mod):
+    """Faraday's law in Stokes form keeps div B = 0 to round-off.  The
+    absorbing layer damps B towards its initial value with an r-dependent
+    rate and is excluded (it is a sink, not part of Eq. 18)."""
+    c = mk(48, 40, "dipole", r_max=12.0, r_lc=4.0)
+    o = oracle_mod.Oracle(c)
+    assert div_b(o) < 1e-13
+    o.step(25)
+    assert div_b(o, r_below=c["r_abs"]) < 1e-12
+    assert np.max(np.abs(o.get("E_th"))) > 0  # the rotating star drives fields
+
+
+def test_vacuum_dipole_curl_free_second_order(oracle_mod):
+    """One Ampere stage on the static vacuum dipole (curl B = 0, J = 0):
+    E/dt is the discrete curl, which must vanish at second order away from
+    the boundaries."""
+    errs = []
+    for n in (32, 64, 128):
+        o = oracle_mod.Oracle(mk(n, n, "dipole", r_max=10.0, r_lc=1e9))
+        o.step(1, oracle_mod.ST["ampere"])
+        rn, _, tn, _ = grid(o)
+        ep = o.get("E_ph") / o.dt
+        sl = slice(n // 8, n // 2)
+        errs.append(np.max(np.abs(ep[sl, 1:-1] * rn[sl, None] ** 4)))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.8, (errs, rates)
+
+
+def michel_cfg(n, allff=True):
+    c = mk(n, n, "michel", r_max=50.0 / 3.0, r_lc=5.0, r_abs=15.0)
+    if allff:
+        c.update(psi_break=[-1.0], f_break=[1.0])  # force-free everywhere
+    return c
+
+
+def test_michel_corotation_boundary_matches_closed_form(oracle_mod):
+    """At r_star the corotation field -(Omega x r) x B / c of Sect. 4 must
+    coincide with Michel's E_theta = B_phi = -(Psi*/R_LC) sin(theta)/r."""
+    o = oracle_mod.Oracle(michel_cfg(64))
+    _, _, _, th = grid(o)
+    et0 = o.get("E_th")[0]
+    assert np.allclose(et0, -(1.0 / 5.0) * np.sin(th), rtol=1e-13, atol=0)
+
+
+def test_michel_perpendicular_current_second_order(oracle_mod):
+    """First term of Eq. 24 at the nodes against Michel's solution:
+    rho = -Psi* Omega cos(theta) / (2 pi c r^2),
+    J_perp = c rho (E x B)/B^2 with E = E_theta, B = (B_r, 0, B_phi)."""
+    errs = []
+    for n in (32, 64, 128):
+        o = oracle_mod.Oracle(michel_cfg(n))
+        o.step(1, oracle_mod.ST["node"])
+        rn, _, tn, _ = grid(o)
+        r, t = rn[:, None], tn[None, :]
+        om = 0.2
+        br, bp = 1.0 / r ** 2, -om * np.sin(t) / r
+        et = bp
+        rho = -om * np.cos(t) / (2 * math.pi * r ** 2)
+        b2 = br ** 2 + bp ** 2
+        jr = rho * et * bp / b2
+        jp = -rho * et * br / b2
+        sl_i, sl_j = slice(n // 8, n // 2), slice(n // 8, n - n // 8)
+        scale = np.abs(rho * r ** 0)[sl_i, sl_j].max()
+        e1 = np.abs(o.get("jperp_r") - jr)[sl_i, sl_j] / scale
+        e2 = np.abs(o.get("jperp_ph") - jp)[sl_i, sl_j] / scale
+        errs.append(max(e1.max(), e2.max()))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert errs[-1] < 1e-2 and min(rates) > 1.7, (errs, rates)
+
+
+def test_michel_force_free_step_is_stationary(oracle_mod):
+    """One force-free step (which includes the renormalisation) leaves the
+    Michel monopole unchanged at O(h^2) per unit time (inside r_abs)."""
+    errs = []
+    for n in (32, 64, 128):
+        o = oracle_mod.Oracle(michel_cfg(n))
+        before = o.fields()
+        o.step(1, oracle_mod.ST["all"] & ~oracle_mod.ST["inject"] & ~oracle_mod.ST["sort"])
+        after = o.fields()
+        rn, _, _, _ = grid(o)
+        iabs = int(np.searchsorted(rn, 14.0))
+        e = 0.0
+        for k in ("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph"):
+            d = (after[k] - before[k])[1:iabs, 1:-1] / o.dt
+            e = max(e, np.max(np.abs(d) * rn[1:iabs, None] ** 2))
+        errs.append(e)
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.5, (errs, rates)
+
+
+def test_force_free_invariants_after_renormalisation(oracle_mod):
+    """With uniform E and B every edge receives the same correction, so after
+    Eqs. 25-26 the collocated fields satisfy E.B = 0 (Eq. 23) and
+    E^2 <= B^2 at every interior node: a second renormalisation is void."""
+    c = mk(16, 14, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    o = oracle_mod.Oracle(c)
+    for k, v in zip(("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph"),
+                    (1.1, -0.4, 2.0, 0.3, 0.9, -0.6)):
+        o.set(k, np.full(o.shape(k), v))
+    o.step(1, oracle_mod.ST["correct"])
+    o.step(1, oracle_mod.ST["correct"])
+    for k in ("dE_r", "dE_th", "dE_ph"):
+        assert np.abs(o.get(k)[3:-3, 3:-3]).max() < 1e-13, k
+
+
+def test_node_renormalisation_closed_form(oracle_mod):
+    """Eqs. 25-26 at one node with uniform collocated fields: E' is E minus
+    its projection on B, then rescaled to |E'| = |B| if it exceeded it."""
+    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    o = oracle_mod.Oracle(c)
+    E = np.array([0.3, -1.7, 0.9])
+    B = np.array([0.5, 0.2, -0.4])
+    for k, v in zip(("E_r", "E_th", "E_ph"), E):
+        o.set(k, np.full(o.shape(k), v))
+    for k, v in zip(("B_r", "B_th", "B_ph"), B):
+        o.set(k, np.full(o.shape(k), v))
+    o.step(1, oracle_mod.ST["correct"])
+    ep = E - E.dot(B) / B.dot(B) * B
+    if ep.dot(ep) > B.dot(B):
+        ep *= math.sqrt(B.dot(B) / ep.dot(ep))
+    got = np.array([o.get(k)[6, 6] for k in ("dE_r", "dE_th", "dE_ph")])
+    assert np.allclose(got, ep - E, rtol=1e-13, atol=1e-14)
+    assert abs((E + got).dot(B)) < 1e-13
+    assert (E + got).dot(E + got) <= B.dot(B) * (1 + 1e-13)
+
+
+def test_michel_spindown_power(oracle_mod):
+    """L(r) of the Michel monopole against L_M = 2 Psi*^2 Omega^2 / 3c
+    (Eq. 35), second-order convergent."""
+    errs = []
+    for n in (32, 64, 128):
+        o = oracle_mod.Oracle(michel_cfg(n))
+        d, prof = o.diagnostics()
+        lm = 2.0 * 0.2 ** 2 / 3.0
+        errs.append(np.max(np.abs(prof[: n // 2] / lm - 1.0)))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert errs[-1] < 1e-3 and min(rates) > 1.8, (errs, rates)
+
+
+def test_blend_table1(oracle_mod):
+    cfg = workloads.config("small_hybrid")
+    o = oracle_mod.Oracle(cfg)
+    u = o.psi_unit
+    assert abs(u - 1.0 / cfg["r_lc"]) < 1e-15
+    for psi, f in [(0.0, 1.0), (0.5, 1.0), (0.85, 1.0), (0.875, 0.5), (0.9, 0.0), (1.5, 0.0),
+                   (2.3, 0.0), (2.35, 0.5), (2.4, 1.0), (10.0, 1.0)]:
+        assert abs(o.blend(psi * u) - f) < 1e-12, psi
+    m = oracle_mod.Oracle(workloads.config("small_michel"))
+    assert m.blend(0.999) == 0.0 and m.blend(1.0) == 1.0 and m.blend(1.5) == 1.0
+
+
+def test_courant_matches_table1_ratio(oracle_mod):
+    """Table 1: dt = 4.3e-9 s and dr = 3.4e2 cm on an 8192^2 log grid over
+    [r*, (10/3) R_LC] with R_LC = 5 r* = 5e6 cm: the oracle's Courant rule
+    (C = 0.5 of the 2D limit at the innermost cell) reproduces both."""
+    c = mk(8192, 8192, "dipole", r_max=50.0 / 3.0, r_lc=5.0, r_abs=15.0)
+    dt_s = oracle_mod.config_dt(c) * 1e6 / 2.99792458e10   # r* = 1e6 cm
+    assert abs(dt_s - 4.3e-9) / 4.3e-9 < 0.02
+    dr = 1e6 * (math.exp(math.log(50.0 / 3.0) / 8192) - 1.0)
+    assert abs(dr - 3.4e2) / 3.4e2 < 0.02
