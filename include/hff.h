@@ -1,0 +1,224 @@
+/*
+ * hff.h -- C ABI of the GB300 (sm_103a) hybrid force-free / particle-in-cell
+ * time step for the axisymmetric aligned pulsar rotator of Soudais, Cerutti &
+ * Contopoulos (2024).
+ *
+ * One call of hff_step advances one or more magnetospheres by whole time
+ * steps on the GPU:
+ *   - flux function Psi as a theta-prefix of B_r (Sect. 3, Eq. 27), FP64
+ *   - blend mask f(Psi) (Eqs. 29-31 generalised to a piecewise-linear table)
+ *   - force-free perpendicular current (first term of Eq. 24)
+ *   - modified Boris push with radiation reaction (Eqs. 15-17), move,
+ *     charge-conserving deposit of J_PIC
+ *   - Yee field advance (Eqs. 18-19) with J = (1-f) J_PIC + f J_FFE (Eq. 28)
+ *   - E renormalisation E.B = 0 and E^2 <= B^2 (Eqs. 25-26) weighted by f
+ *   - corotating star and absorbing layer (Sect. 4), surface pair injection
+ *     (Sects. 4 and 5.1), stable tile sort of the particles.
+ *
+ * Units are Gaussian with c = 1.  Grid: nr x nt cells, r log-spaced on
+ * [r_min, r_max], theta uniform on [0, pi].  Field arrays are row-major with
+ * the theta index fastest:
+ *   which  name   location         shape
+ *   0      E_r    (i+1/2, j)       nr     x (nt+1)
+ *   1      E_th   (i, j+1/2)       (nr+1) x nt
+ *   2      E_ph   (i, j)           (nr+1) x (nt+1)
+ *   3      B_r    (i, j+1/2)       (nr+1) x nt
+ *   4      B_th   (i+1/2, j)       nr     x (nt+1)
+ *   5      B_ph   (i+1/2, j+1/2)   nr     x nt
+ *   6..8   J_r, J_th, J_ph of the last particle deposit (E locations)
+ *   9      Psi at the nodes        (nr+1) x (nt+1), always FP64
+ *   10..12 J_perp at the nodes     (nr+1) x (nt+1)
+ *   13..15 Delta E at the nodes    (nr+1) x (nt+1)
+ * Field values are FP32 (HFF_FP32) or FP64 (HFF_FP64) as configured.
+ *
+ * Particles (per species, structure of arrays): int32 cell = i * nt + j
+ * (-1 = removed), offsets xo, yo in [0, 1) inside the cell in the logical
+ * (ln r, theta) coordinates, u_r, u_th, u_ph = gamma v / c in the local
+ * spherical basis, and the macro-particle weight w; all but cell are in the
+ * configured precision.
+ *
+ * Memory and streams: the caller owns all device memory.  hff_plan reports the
+ * bytes one instance needs; the caller allocates them (for instance as a torch
+ * uint8 tensor), passes them to hff_init and keeps them alive until
+ * hff_destroy returns.  The library allocates no device memory of its own
+ * apart from CUDA graphs.  All work is queued on the caller's stream.
+ *
+ * Errors: every function returns HFF_OK (0) or a negative HFF_ERR_* code;
+ * hff_last_error() gives a message for the calling thread.  Faults detected on
+ * the device (capacity overflow, non-finite particles) are latched in a status
+ * word and reported by hff_status.
+ */
+#ifndef HFF_H
+#define HFF_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HFF_OK 0
+#define HFF_ERR_ARG (-1)       /* invalid argument or configuration        */
+#define HFF_ERR_CAPACITY (-2)  /* particle or memory capacity exceeded     */
+#define HFF_ERR_CUDA (-3)      /* a CUDA call failed                       */
+#define HFF_ERR_TIMEOUT (-4)   /* a bounded device wait gave up            */
+#define HFF_ERR_NONFINITE (-5) /* non-finite values were met on the device */
+
+/* initial field geometry */
+#define HFF_GEOM_DIPOLE 0   /* Psi = mu sin^2(theta) / r (Eq. 37)                 */
+#define HFF_GEOM_MONOPOLE 1 /* Psi = Psi* (1 - cos theta) (Eq. 32)                */
+#define HFF_GEOM_SYNTH 2    /* dipole inside R_LC, split monopole outside          */
+#define HFF_GEOM_UNIFORM 3  /* Psi = B0 r^2 sin^2(theta) / 2 (test field)          */
+#define HFF_GEOM_MICHEL 4   /* Michel monopole with B_ph and E_th (Eqs. 32-33)     */
+
+#define HFF_FP32 0
+#define HFF_FP64 1
+
+#define HFF_HOST 0
+#define HFF_DEVICE 1
+
+/* stage bits of hff_step_stages (a full step runs all, in this order) */
+#define HFF_ST_NODE 1      /* Psi, J_perp, per-cell force-free flag              */
+#define HFF_ST_CORRECT 2   /* Delta E at the nodes and E += f <Delta E>          */
+#define HFF_ST_PUSH 4      /* push, move, deposit                               */
+#define HFF_ST_FARADAY1 8  /* B^n -> B^{n+1/2}                                  */
+#define HFF_ST_AMPERE 16   /* E^n -> E^{n+1}, boundaries, absorber on E          */
+#define HFF_ST_FARADAY2 32 /* B^{n+1/2} -> B^{n+1}, absorber on B                */
+#define HFF_ST_INJECT 64   /* surface pair injection                            */
+#define HFF_ST_SORT 128    /* stable tile sort + compaction (on its cadence)     */
+#define HFF_ST_ALL 255
+/* order of execution: NODE, PUSH, FARADAY1, AMPERE, CORRECT, FARADAY2,
+ * INJECT, SORT */
+
+/* scalars for hff_set_scalar */
+#define HFF_SCALAR_RR_SCALE 0 /* ramp multiplier of the radiation reaction (Sect. 5.1) */
+
+typedef struct hff_config {
+  int32_t nr, nt;           /* cells in r and theta (each >= 8)                  */
+  double r_min, r_max;      /* radial extent; r_min is the stellar radius        */
+  double r_lc;              /* light-cylinder radius; Omega = c / r_lc (Eq. 1)   */
+  double b_star;            /* surface field scale: mu = b_star r_min^3          */
+  int32_t geom;             /* HFF_GEOM_*                                         */
+  double courant;           /* fraction of the 2D CFL limit, (0, 0.9]            */
+  double r_abs;             /* start of the absorbing layer (Sect. 4: 3 R_LC)    */
+  double absorb_strength;   /* damping per step at r_max (cubic ramp from r_abs) */
+  int32_t n_breaks;         /* 0..4 breakpoints of f; 0 means f = 0 (pure PIC)   */
+  double psi_break[4];      /* in units of Psi_pc = mu/R_LC (dipolar fields) or
+                               Psi* = b_star r_min^2 (monopoles), ascending      */
+  double f_break[4];        /* f at each breakpoint                              */
+  int32_t n_species;        /* 1..4; species 0 and 1 form the injected pairs     */
+  double q[4], m[4];        /* charge (units of e) and mass                      */
+  int32_t inject;           /* 1 = surface top-up injection on                   */
+  double kappa_inj;         /* injected multiplicity (Sect. 4: 10)               */
+  double w_inj;             /* weight of an injected macro-particle              */
+  double gamma_rad;         /* radiation-reaction Lorentz factor, 0 = off        */
+  double b_ref;             /* field at which gamma_rad is quoted                */
+  double rr_scale;          /* initial ramp multiplier (see HFF_SCALAR_RR_SCALE) */
+  double shell_r;           /* u_perp removed below this radius (Sect. 5.1)      */
+  double synth_psi_open;    /* HFF_GEOM_SYNTH open flux in units of Psi_pc       */
+  uint64_t seed;            /* key of the injection generator                    */
+  int64_t capacity;         /* particle slots per species                        */
+  int32_t tile_r, tile_t;   /* sort tile in cells (0 = default 16 x 32)          */
+  int32_t sort_every;       /* sort cadence in steps, 1..8 (0 = never sort)      */
+  int32_t precision;        /* HFF_FP32 or HFF_FP64                              */
+} hff_config;
+
+typedef struct hff_info {
+  double dt;                /* time step (Courant rule of the config)            */
+  double psi_unit;          /* Psi_pc or Psi* in code units                      */
+  int64_t step;             /* steps taken                                       */
+  int64_t count[4];         /* particle slots in use per species (incl. removed) */
+  int32_t tile_r, tile_t, sort_every, precision;
+  int64_t kernels_per_step; /* kernels one step launches (sort steps: more)      */
+  int64_t kernels_launched; /* kernels launched by hff_step since hff_init       */
+} hff_info;
+
+typedef struct hff_particle_view {
+  int64_t n;                /* slots in use (removed particles have cell < 0)    */
+  int32_t *cell;            /* device pointers, valid until the next hff_step    */
+  void *xo, *yo, *ur, *ut, *up, *w;
+} hff_particle_view;
+
+typedef struct hff_diag {
+  double psi_open;          /* Psi at (node row nearest 2 R_LC, theta = pi/2)    */
+  double eps;               /* |L_in - L_out| / L_out (Eq. 36)                   */
+  double l_in, l_out;       /* L averaged over [r_min, 2 r_min] and [2, 3] R_LC  */
+  double gauss_max, gauss_rms, rho_max; /* |div E/4pi - rho| on interior nodes   */
+  double u_e, u_b;          /* field energies (1/8pi) int E^2, B^2 dV            */
+  double kinetic[4];        /* sum w m (gamma - 1) per species                   */
+  double count[4];          /* live particles per species                        */
+  double injected, killed, radiated, nonfinite; /* running totals (weights)      */
+} hff_diag;
+
+typedef struct hff_handle hff_handle;
+
+/* Device bytes one instance of cfg needs (Sect. 4 grid, Sect. 3 particles).
+ * n_inst must be 1.  Returns HFF_ERR_ARG for an invalid configuration. */
+int hff_plan(const hff_config *cfg, int n_inst, size_t *bytes);
+
+/* Initialise an instance in caller-owned device memory dev_mem (>= the
+ * planned bytes, 256-byte aligned) on the CUDA stream `stream` (cudaStream_t,
+ * may be NULL for the legacy stream).  Builds the geometry in FP64 on the host,
+ * the initial B from the analytic flux function of cfg->geom (Eqs. 32, 37) by
+ * exact-area differences, E = 0 except the corotating star (Sect. 4), and no
+ * particles.  *out receives a handle owned by the caller (free with
+ * hff_destroy).  n_inst must be 1. */
+int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, void *stream,
+             hff_handle **out);
+
+/* Replace the particles of one species by n particles (SoA arrays as described
+ * above; `where` = HFF_HOST or HFF_DEVICE says where the source arrays live).
+ * Values must be in the configured precision.  The particles are sorted by
+ * tile if sorting is enabled.  HFF_ERR_CAPACITY if n > capacity. */
+int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const int32_t *cell,
+                       const void *xo, const void *yo, const void *ur, const void *ut,
+                       const void *up, const void *w, int where);
+
+/* Overwrite field `which` (0..5) with `bytes` bytes from src (host or device).
+ * The initial-B reference of the absorber is not changed. */
+int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where);
+
+/* Copy field `which` (0..15, see the table above) into dst (host or device,
+ * `bytes` must equal the field size).  which = 9 computes Psi (Eq. 27) in FP64
+ * from the current B_r.  Synchronises the stream. */
+int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int where);
+
+/* Advance nsteps whole steps (asynchronous on the stream; one CUDA graph per
+ * step, replayed).  Returns the latched device status of earlier steps. */
+int hff_step(hff_handle *h, int32_t nsteps);
+
+/* Advance nsteps steps running only the stages in the HFF_ST_* mask (eager
+ * launches; used to test the parts of a step). */
+int hff_step_stages(hff_handle *h, int32_t nsteps, int32_t stages);
+
+/* Set a per-step scalar (HFF_SCALAR_*).  The value is copied to the device
+ * on the stream, so it takes effect for the steps queued after the call. */
+int hff_set_scalar(hff_handle *h, int which, double value);
+
+/* Device views of one species' particles (valid until the next hff_step).
+ * Synchronises the stream to read the count. */
+int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out);
+
+/* FP64 diagnostics of Sect. 4: spin-down L(r) (Eq. 35) at every half-node row
+ * into l_prof (nr doubles on the host, may be NULL), the dissipation rate of
+ * Eq. 36, the open flux, Gauss's law residual, energies and counters.
+ * Synchronises the stream. */
+int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof);
+
+/* Step counter, time step, counts and the tile / precision choices. */
+int hff_get_info(hff_handle *h, hff_info *out);
+
+/* Read and clear the latched device status: HFF_OK, HFF_ERR_CAPACITY or
+ * HFF_ERR_NONFINITE.  Synchronises the stream. */
+int hff_status(hff_handle *h);
+
+/* Release the handle and its CUDA graphs (not the caller's memory). */
+int hff_destroy(hff_handle *h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *hff_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -99,6 +99,7 @@ def lib():
         L.or_inject_target.argtypes = [vp, C.c_int]
         L.or_set_rr_scale.argtypes = [vp, d]
         L.or_step.argtypes = [vp, i32, i32]
+        L.or_sort_now.argtypes = [vp]
         L.or_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
         L.or_node_charge.argtypes = [vp, vp]
         L.or_push_local.argtypes = [d, d, d, pd, pd, pd, pd, pd]
@@ -220,6 +221,9 @@ class Oracle:
 
     def step(self, n: int = 1, stages: int = 255) -> None:
         self.L.or_step(self.h, n, stages)
+
+    def sort_now(self) -> None:
+        self.L.or_sort_now(self.h)
 
     def set_rr_scale(self, v: float) -> None:
         self.L.or_set_rr_scale(self.h, v)

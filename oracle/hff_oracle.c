@@ -858,6 +858,12 @@ static void sort_species(ost *s, int sp) {
   s->n[sp] = live;
 }
 
+int or_sort_now(void *st) {
+  ost *s = (ost *)st;
+  for (int sp = 0; sp < s->c.n_species; ++sp) sort_species(s, sp);
+  return 0;
+}
+
 int or_step(void *st, int32_t nsteps, int32_t stages) {
   ost *s = (ost *)st;
   for (int32_t n = 0; n < nsteps; ++n) {

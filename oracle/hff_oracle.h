@@ -114,6 +114,8 @@ int32_t or_inject_target(void *st, int j);
 
 void or_set_rr_scale(void *st, double v);
 int or_step(void *st, int32_t nsteps, int32_t stages);
+/* Stable tile sort of every species now, without advancing the step. */
+int or_sort_now(void *st);
 
 /* Diagnostics (Sect. 4): L(r) at every half-node row r_{i+1/2} into l_prof
  * (nr values, may be NULL). */

@@ -1,0 +1,886 @@
+// api.cu -- the C ABI of include/hff.h: memory plan in caller-owned device
+// memory, FP64 host geometry and initial fields, the step as CUDA graphs
+// (one per particle-buffer parity, plus the sort), and the read-side calls.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hff.h"
+#include "diag.cuh"
+#include "hff_common.cuh"
+
+using namespace hff;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &m) {
+  g_err = m;
+  return code;
+}
+
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) return fail(HFF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int kChunk = 8192;  // particles per work item of the tiled push
+
+// ------------------------------------------------------------------ geometry
+// FP64 grid of Sect. 4: r log-spaced, theta uniform, geometric half nodes,
+// dual cells clipped at r_min, r_max and the axis; exact-integral measures.
+struct Geom {
+  int nr, nt;
+  double r_min, r_max, dlog, dth;
+  double rn(int i) const { return r_min * std::exp(i * dlog); }
+  double rh(int i) const { return r_min * std::exp((i + 0.5) * dlog); }
+  double tn(int j) const { return j * dth; }
+  double th(int j) const { return (j + 0.5) * dth; }
+  double rlo(int i) const { return i == 0 ? r_min : rh(i - 1); }
+  double rhi(int i) const { return i == nr ? r_max : rh(i); }
+  double tlo(int j) const { return j == 0 ? 0.0 : th(j - 1); }
+  double thi(int j) const { return j == nt ? kPi : th(j); }
+  double dcp(int j) const { return std::cos(tn(j)) - std::cos(tn(j + 1)); }
+  double dch(int j) const { return std::cos(tlo(j)) - std::cos(thi(j)); }
+  double a_br(int i, int j) const { return 2 * kPi * rn(i) * rn(i) * dcp(j); }
+  double a_bt(int i, int j) const { return kPi * std::sin(tn(j)) * (rn(i + 1) * rn(i + 1) - rn(i) * rn(i)); }
+};
+
+double courant_dt(const hff_config &c) {
+  const double dlog = std::log(c.r_max / c.r_min) / c.nr, dth = kPi / c.nt;
+  double best = 1e300;
+  for (int i = 0; i < c.nr; ++i) {
+    const double r0 = c.r_min * std::exp(i * dlog), r1 = c.r_min * std::exp((i + 1) * dlog);
+    const double dr = r1 - r0, rt = r0 * dth;
+    const double l = 1.0 / std::sqrt(1.0 / (dr * dr) + 1.0 / (rt * rt));
+    if (l < best) best = l;
+  }
+  return c.courant * best;
+}
+
+double psi_unit_of(const hff_config &c) {
+  if (c.geom == HFF_GEOM_MONOPOLE || c.geom == HFF_GEOM_MICHEL) return c.b_star * c.r_min * c.r_min;
+  return c.b_star * c.r_min * c.r_min * c.r_min / c.r_lc;
+}
+
+// blend of Eqs. 29-31 in FP64 on the host (injection eligibility at init)
+double blend_host(const hff_config &c, double unit, double psi) {
+  const int n = c.n_breaks;
+  if (n <= 0) return 0.0;
+  if (psi < c.psi_break[0] * unit) return c.f_break[0];
+  for (int k = 1; k < n; ++k) {
+    const double x0 = c.psi_break[k - 1] * unit, x1 = c.psi_break[k] * unit;
+    if (psi < x1) return c.f_break[k - 1] + (c.f_break[k] - c.f_break[k - 1]) * (psi - x0) / (x1 - x0);
+  }
+  return c.f_break[n - 1];
+}
+
+// analytic flux functions of the initial fields (Eqs. 32 and 37)
+double psi_analytic(const hff_config &c, double unit, double r, double t) {
+  const double mu = c.b_star * c.r_min * c.r_min * c.r_min, pst = c.b_star * c.r_min * c.r_min;
+  const double sn = std::sin(t), cs = std::cos(t);
+  switch (c.geom) {
+    case HFF_GEOM_DIPOLE: return mu * sn * sn / r;
+    case HFF_GEOM_MONOPOLE:
+    case HFF_GEOM_MICHEL: return pst * (1.0 - cs);
+    case HFF_GEOM_UNIFORM: return 0.5 * c.b_star * r * r * sn * sn;
+    case HFF_GEOM_SYNTH: {
+      const double w = 0.5 * (1.0 - std::tanh((r - c.r_lc) / (0.2 * c.r_lc)));
+      return w * mu * sn * sn / r + (1.0 - w) * c.synth_psi_open * unit * (1.0 - std::fabs(cs));
+    }
+  }
+  return 0.0;
+}
+
+int validate(const hff_config *c) {
+  if (!c) return fail(HFF_ERR_ARG, "null config");
+  if (c->nr < 8 || c->nt < 8) return fail(HFF_ERR_ARG, "nr and nt must be >= 8");
+  if ((int64_t)(c->nr + 1) * (c->nt + 1) > (int64_t)1 << 31) return fail(HFF_ERR_ARG, "grid too large");
+  if (!(c->r_min > 0 && c->r_max > c->r_min && c->r_lc > 0)) return fail(HFF_ERR_ARG, "bad radii");
+  if (!(c->courant > 0 && c->courant <= 0.9)) return fail(HFF_ERR_ARG, "courant must be in (0, 0.9]");
+  if (c->geom < 0 || c->geom > 4) return fail(HFF_ERR_ARG, "bad geom");
+  if (c->n_breaks < 0 || c->n_breaks > 4) return fail(HFF_ERR_ARG, "n_breaks must be 0..4");
+  for (int k = 1; k < c->n_breaks; ++k)
+    if (c->psi_break[k] < c->psi_break[k - 1]) return fail(HFF_ERR_ARG, "psi_break must ascend");
+  if (c->n_species < 1 || c->n_species > 4) return fail(HFF_ERR_ARG, "n_species must be 1..4");
+  for (int s = 0; s < c->n_species; ++s)
+    if (!(c->m[s] > 0)) return fail(HFF_ERR_ARG, "masses must be positive");
+  if (c->capacity < 0 || c->capacity > 2000000000LL) return fail(HFF_ERR_ARG, "capacity out of range");
+  if (c->sort_every < 0 || c->sort_every > 8) return fail(HFF_ERR_ARG, "sort_every must be 0..8");
+  if (c->precision != HFF_FP32 && c->precision != HFF_FP64) return fail(HFF_ERR_ARG, "bad precision");
+  const double dlog = std::log(c->r_max / c->r_min) / c->nr;
+  const double xi_abs = std::log(c->r_abs / c->r_min) / dlog;
+  if (!(c->r_abs > c->r_min) || xi_abs > c->nr - 3) return fail(HFF_ERR_ARG, "r_abs must lie >= 3 cells inside r_max");
+  if (c->tile_r < 0 || c->tile_t < 0 || c->tile_r > 64 || c->tile_t > 128)
+    return fail(HFF_ERR_ARG, "tile out of range");
+  return HFF_OK;
+}
+
+// ----------------------------------------------------------- memory layout
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = (off + 255) & ~size_t(255);
+    off = o + bytes;
+    return o;
+  }
+};
+
+struct Offsets {
+  size_t f[19];          // er et ep br bt bp br0 bt0 bp0 jr jt jp psi jpr jpt jpp der det dep
+  size_t ffcell;
+  size_t tab_r[16];      // rn inv_rn rh inv_rh c_b2 c_bp2 c_e2 c_ep2 rho_a rho_b rh2 dep_r dep_t dep_p sig_n sig_h
+  size_t tab_c[5];       // sn sh inv_sh inv_dcp inv_dch
+  size_t r2n, dcp;       // FP64 prefix factors
+  size_t dg[9];          // FP64 diag geometry: rn rh rlo rhi sn sh dch tlo thi
+  size_t part[2][kMaxSpecies][7];
+  size_t small;          // counters block
+  size_t surf, target, inj_prefix;
+  size_t keys_a, keys_b, idx_a, idx_b, hist, spart, tstart, tend;
+  size_t items;
+  size_t qnode, rows, psi64;
+  int ntiles, ntt, max_items, nb, nparts;
+  size_t total;
+};
+
+struct Small {  // device counters, one 256-byte block
+  long long count[kMaxSpecies];
+  long long count_sorted[kMaxSpecies];
+  long long inj_base[kMaxSpecies];
+  long long step;
+  double acc[4];
+  double rr;
+  double kin[kMaxSpecies];
+  double cnt[kMaxSpecies];
+  unsigned status;
+  int n_items;
+  int next;
+};
+
+int tile_r_of(const hff_config &c) { return c.tile_r > 0 ? c.tile_r : 16; }
+int tile_t_of(const hff_config &c) { return c.tile_t > 0 ? c.tile_t : 32; }
+
+void layout(const hff_config &c, Offsets &o) {
+  Layout L;
+  const size_t R = c.precision == HFF_FP64 ? 8 : 4;
+  const size_t nr = c.nr, nt = c.nt, nn = (nr + 1) * (nt + 1);
+  const size_t sz[19] = {nr * (nt + 1), (nr + 1) * nt, nn, (nr + 1) * nt, nr * (nt + 1), nr * nt,
+                         (nr + 1) * nt, nr * (nt + 1), nr * nt, nr * (nt + 1), (nr + 1) * nt, nn,
+                         nn, nn, nn, nn, nn, nn, nn};
+  for (int k = 0; k < 19; ++k) o.f[k] = L.take(sz[k] * R);
+  o.ffcell = L.take(nr * nt);
+  const size_t rl[16] = {nr + 1, nr + 1, nr, nr, nr, nr, nr + 1, nr + 1, nr + 1, nr + 1, nr, nr, nr + 1, nr + 1, nr + 1, nr};
+  for (int k = 0; k < 16; ++k) o.tab_r[k] = L.take(rl[k] * R);
+  const size_t cl[5] = {nt + 1, nt, nt, nt, nt + 1};
+  for (int k = 0; k < 5; ++k) o.tab_c[k] = L.take(cl[k] * R);
+  o.r2n = L.take((nr + 1) * 8);
+  o.dcp = L.take(nt * 8);
+  const size_t dl[9] = {nr + 1, nr, nr + 1, nr + 1, nt + 1, nt, nt + 1, nt + 1, nt + 1};
+  for (int k = 0; k < 9; ++k) o.dg[k] = L.take(dl[k] * 8);
+  const size_t cap = (size_t)c.capacity;
+  const int parities = c.sort_every > 0 ? 2 : 1;
+  std::memset(o.part, 0, sizeof(o.part));
+  for (int p = 0; p < parities; ++p)
+    for (int s = 0; s < c.n_species; ++s) {
+      o.part[p][s][0] = L.take(cap * 4);
+      for (int k = 1; k < 7; ++k) o.part[p][s][k] = L.take(cap * R);
+    }
+  o.small = L.take(sizeof(Small));
+  o.surf = L.take(nt * 4);
+  o.target = L.take(nt * 4);
+  o.inj_prefix = L.take((nt + 1) * 4);
+  const int tr = tile_r_of(c), tt = tile_t_of(c);
+  o.ntt = (int)((nt + tt - 1) / tt);
+  o.ntiles = (int)((nr + tr - 1) / tr) * o.ntt;
+  o.nb = (int)((cap + 2047) / 2048);
+  o.nparts = (int)(((size_t)o.nb * 256 + 4095) / 4096);
+  o.max_items = c.n_species * (o.ntiles + (int)((cap + kChunk - 1) / kChunk)) + 1;
+  if (c.sort_every > 0) {
+    o.keys_a = L.take(cap * 4); o.keys_b = L.take(cap * 4);
+    o.idx_a = L.take(cap * 4); o.idx_b = L.take(cap * 4);
+    o.hist = L.take((size_t)o.nb * 256 * 4 + 4);
+    o.spart = L.take((size_t)o.nparts * 4 + 4);
+    o.tstart = L.take(((size_t)o.ntiles + 1) * 4);
+    o.tend = L.take(((size_t)o.ntiles + 1) * 4);
+    o.items = L.take((size_t)o.max_items * sizeof(int4));
+  }
+  o.qnode = L.take(nn * 8);
+  o.rows = L.take((nr + 1) * 8 * 8);
+  o.psi64 = L.take(nn * 8);
+  o.total = (L.off + 255) & ~size_t(255);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct hff_handle {
+  hff_config c;
+  cudaStream_t st = nullptr, cap_st = nullptr;
+  char *base = nullptr;
+  Offsets o;
+  Geom g;
+  double dt = 0, psi_unit = 0, xi_abs = 0;
+  int halo = 0, push_grid = 0, tail_grid = 0;
+  Params<float> pf[2];
+  Params<double> pd[2];
+  WorkList wl{};
+  SortScratch ss{};
+  DiagGeom dg{};
+  Small *small = nullptr;
+  int parity = 0;
+  int64_t step = 0;
+  cudaGraphExec_t g_step[2] = {nullptr, nullptr}, g_sort[2] = {nullptr, nullptr};
+  int64_t k_step[2] = {0, 0}, k_sort[2] = {0, 0};
+  int64_t launched = 0;
+};
+
+namespace {
+
+template <typename R> Params<R> *params(hff_handle *h);
+template <> Params<float> *params<float>(hff_handle *h) { return h->pf; }
+template <> Params<double> *params<double>(hff_handle *h) { return h->pd; }
+
+template <typename R>
+void fill_params(hff_handle *h) {
+  const hff_config &c = h->c;
+  const Offsets &o = h->o;
+  char *b = h->base;
+  for (int par = 0; par < 2; ++par) {
+    Params<R> &p = params<R>(h)[par];
+    std::memset(&p, 0, sizeof(p));
+    p.nr = c.nr; p.nt = c.nt;
+    p.dt = (R)h->dt; p.dlog = (R)h->g.dlog; p.dth = (R)h->g.dth; p.omega = (R)(1.0 / c.r_lc);
+    p.r_min = (R)c.r_min; p.xi_abs = (R)h->xi_abs; p.shell_r2 = (R)(c.shell_r * c.shell_r);
+    p.n_breaks = c.n_breaks;
+    for (int k = 0; k < kMaxBreaks; ++k) {
+      p.psi_break[k] = (R)(c.psi_break[k] * h->psi_unit);
+      p.f_break[k] = (R)c.f_break[k];
+    }
+    p.n_species = c.n_species;
+    for (int s = 0; s < c.n_species; ++s) {
+      p.q[s] = (R)c.q[s]; p.m[s] = (R)c.m[s]; p.qm[s] = (R)(c.q[s] / c.m[s]);
+      // radiation-reaction strength (Eq. 16 enters du/dt as g / (m c)):
+      // (2/3) r_0^2 = |q_0| / (gamma_rad^2 b_ref) for species 0, scaled by the
+      // classical radius r_s = q_s^2 / m_s of the others
+      double k = 0.0;
+      if (c.gamma_rad > 0) {
+        const double r0c = c.q[0] * c.q[0] / c.m[0], rsc = c.q[s] * c.q[s] / c.m[s];
+        const double two3 = std::fabs(c.q[0]) / (c.gamma_rad * c.gamma_rad * c.b_ref);
+        k = two3 * (rsc / r0c) * (rsc / r0c) / c.m[s];
+      }
+      p.krr[s] = (R)k;
+    }
+    Tables<R> &t = p.t;
+    const R **tr[16] = {&t.rn, &t.inv_rn, &t.rh, &t.inv_rh, &t.c_b2, &t.c_bp2, &t.c_e2, &t.c_ep2,
+                        &t.rho_a, &t.rho_b, &t.rh2, &t.dep_r, &t.dep_t, &t.dep_p, &t.sig_n, &t.sig_h};
+    for (int k = 0; k < 16; ++k) *tr[k] = reinterpret_cast<const R *>(b + o.tab_r[k]);
+    const R **tc[5] = {&t.sn, &t.sh, &t.inv_sh, &t.inv_dcp, &t.inv_dch};
+    for (int k = 0; k < 5; ++k) *tc[k] = reinterpret_cast<const R *>(b + o.tab_c[k]);
+    t.r2n = reinterpret_cast<const double *>(b + o.r2n);
+    t.dcp = reinterpret_cast<const double *>(b + o.dcp);
+    Fields<R> &f = p.f;
+    R **fp[19] = {&f.er, &f.et, &f.ep, &f.br, &f.bt, &f.bp, &f.br0, &f.bt0, &f.bp0, &f.jr, &f.jt, &f.jp,
+                  &f.psi, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep};
+    for (int k = 0; k < 19; ++k) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
+    f.ffcell = reinterpret_cast<uint8_t *>(b + o.ffcell);
+    const int pp = (c.sort_every > 0) ? par : 0;
+    for (int s = 0; s < c.n_species; ++s) {
+      p.sp[s].cell = reinterpret_cast<int32_t *>(b + o.part[pp][s][0]);
+      R **q[6] = {&p.sp[s].xo, &p.sp[s].yo, &p.sp[s].ur, &p.sp[s].ut, &p.sp[s].up, &p.sp[s].w};
+      for (int k = 0; k < 6; ++k) *q[k] = reinterpret_cast<R *>(b + o.part[pp][s][k + 1]);
+    }
+    p.cap = c.capacity;
+    p.count = h->small->count;
+    p.count_sorted = h->small->count_sorted;
+    p.rr_scale = &h->small->rr;
+    p.surf = reinterpret_cast<int32_t *>(b + o.surf);
+    p.target = reinterpret_cast<const int32_t *>(b + o.target);
+    p.inj_prefix = reinterpret_cast<int32_t *>(b + o.inj_prefix);
+    p.inj_base = h->small->inj_base;
+    p.step = &h->small->step;
+    p.seed_lo = (uint32_t)c.seed;
+    p.seed_hi = (uint32_t)(c.seed >> 32);
+    p.inject = c.inject;
+    p.w_inj = (R)c.w_inj;
+    p.acc = h->small->acc;
+    p.status = &h->small->status;
+    p.tile_r = tile_r_of(c); p.tile_t = tile_t_of(c); p.ntt = o.ntt;
+  }
+}
+
+template <typename R>
+int upload(hff_handle *h, size_t off, const std::vector<double> &v) {
+  std::vector<R> tmp(v.begin(), v.end());
+  CK(cudaMemcpyAsync(h->base + off, tmp.data(), tmp.size() * sizeof(R), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+int upload_d(hff_handle *h, size_t off, const std::vector<double> &v) {
+  CK(cudaMemcpyAsync(h->base + off, v.data(), v.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+double sigma_abs(const hff_config &c, double r) {
+  if (r <= c.r_abs) return 0.0;
+  const double x = (r - c.r_abs) / (c.r_max - c.r_abs);
+  return c.absorb_strength * x * x * x;
+}
+
+template <typename R>
+int init_state(hff_handle *h) {
+  const hff_config &c = h->c;
+  const Geom &g = h->g;
+  const int nr = c.nr, nt = c.nt;
+  const double dt = h->dt;
+  int rc;
+  // row tables
+  std::vector<double> T[16];
+  for (auto &v : T) v.clear();
+  for (int i = 0; i <= nr; ++i) {
+    const double lo = g.rlo(i), hi = g.rhi(i);
+    T[0].push_back(g.rn(i));
+    T[1].push_back(1.0 / g.rn(i));
+    T[6].push_back(2.0 / (hi * hi - lo * lo));
+    T[7].push_back(2.0 * (hi - lo) / ((hi * hi - lo * lo) * g.dth));
+    T[8].push_back(3.0 / (4 * kPi * (hi * hi * hi - lo * lo * lo)));
+    T[9].push_back(3.0 * (hi * hi - lo * lo) / (8 * kPi * (hi * hi * hi - lo * lo * lo)));
+    T[12].push_back(1.0 / (kPi * (hi * hi - lo * lo) * dt));
+    T[13].push_back(3.0 / (2 * kPi * (hi * hi * hi - lo * lo * lo)));
+    T[14].push_back(sigma_abs(c, g.rn(i)));
+  }
+  for (int i = 0; i < nr; ++i) {
+    const double a = g.rn(i), b = g.rn(i + 1);
+    T[2].push_back(g.rh(i));
+    T[3].push_back(1.0 / g.rh(i));
+    T[4].push_back(2.0 / (b * b - a * a));
+    T[5].push_back(2.0 * (b - a) / ((b * b - a * a) * g.dth));
+    T[10].push_back(g.rh(i) * g.rh(i));
+    T[11].push_back(1.0 / (2 * kPi * g.rh(i) * g.rh(i) * dt));
+    T[15].push_back(sigma_abs(c, g.rh(i)));
+  }
+  for (int k = 0; k < 16; ++k)
+    if ((rc = upload<R>(h, h->o.tab_r[k], T[k])) != HFF_OK) return rc;
+  std::vector<double> C[5];
+  for (int j = 0; j <= nt; ++j) {
+    C[0].push_back(std::sin(g.tn(j)));
+    C[4].push_back(1.0 / g.dch(j));
+  }
+  for (int j = 0; j < nt; ++j) {
+    C[1].push_back(std::sin(g.th(j)));
+    C[2].push_back(1.0 / std::sin(g.th(j)));
+    C[3].push_back(1.0 / g.dcp(j));
+  }
+  for (int k = 0; k < 5; ++k)
+    if ((rc = upload<R>(h, h->o.tab_c[k], C[k])) != HFF_OK) return rc;
+  std::vector<double> r2n, dcp;
+  for (int i = 0; i <= nr; ++i) r2n.push_back(g.rn(i) * g.rn(i));
+  for (int j = 0; j < nt; ++j) dcp.push_back(g.dcp(j));
+  if ((rc = upload_d(h, h->o.r2n, r2n)) != HFF_OK) return rc;
+  if ((rc = upload_d(h, h->o.dcp, dcp)) != HFF_OK) return rc;
+  {  // FP64 diagnostic geometry
+    std::vector<double> D[9];
+    for (int i = 0; i <= nr; ++i) { D[0].push_back(g.rn(i)); D[2].push_back(g.rlo(i)); D[3].push_back(g.rhi(i)); }
+    for (int i = 0; i < nr; ++i) D[1].push_back(g.rh(i));
+    for (int j = 0; j <= nt; ++j) {
+      D[4].push_back(std::sin(g.tn(j))); D[6].push_back(g.dch(j));
+      D[7].push_back(g.tlo(j)); D[8].push_back(g.thi(j));
+    }
+    for (int j = 0; j < nt; ++j) D[5].push_back(std::sin(g.th(j)));
+    for (int k = 0; k < 9; ++k)
+      if ((rc = upload_d(h, h->o.dg[k], D[k])) != HFF_OK) return rc;
+    const double **dp[9] = {&h->dg.rn, &h->dg.rh, &h->dg.rlo, &h->dg.rhi, &h->dg.sn, &h->dg.sh, &h->dg.dch,
+                            &h->dg.tlo, &h->dg.thi};
+    for (int k = 0; k < 9; ++k) *dp[k] = reinterpret_cast<const double *>(h->base + h->o.dg[k]);
+    h->dg.dcp = reinterpret_cast<const double *>(h->base + h->o.dcp);
+    h->dg.dth = g.dth;
+    int imax = (int)std::floor(h->xi_abs) - 2;
+    if (imax > nr - 2) imax = nr - 2;
+    h->dg.imax = imax;
+  }
+  // initial B from the analytic flux function by exact-area differences
+  // (B = grad Psi x phi / (r sin theta)), so that div B = 0 exactly
+  const double unit = h->psi_unit;
+  std::vector<double> br((size_t)(nr + 1) * nt), bt((size_t)nr * (nt + 1), 0.0), bp((size_t)nr * nt, 0.0);
+  std::vector<double> er((size_t)nr * (nt + 1), 0.0), et((size_t)(nr + 1) * nt, 0.0), ep((size_t)(nr + 1) * (nt + 1), 0.0);
+  for (int i = 0; i <= nr; ++i)
+    for (int j = 0; j < nt; ++j)
+      br[(size_t)i * nt + j] = (psi_analytic(c, unit, g.rn(i), g.tn(j + 1)) - psi_analytic(c, unit, g.rn(i), g.tn(j))) *
+                               2 * kPi / g.a_br(i, j);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 1; j < nt; ++j)
+      bt[(size_t)i * (nt + 1) + j] =
+          -(psi_analytic(c, unit, g.rn(i + 1), g.tn(j)) - psi_analytic(c, unit, g.rn(i), g.tn(j))) * 2 * kPi / g.a_bt(i, j);
+  if (c.geom == HFF_GEOM_MICHEL) {  // Eq. 33 and E_theta = B_phi
+    const double pst = c.b_star * c.r_min * c.r_min;
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nt; ++j) bp[(size_t)i * nt + j] = -(pst / c.r_lc) * std::sin(g.th(j)) / g.rh(i);
+    for (int i = 0; i <= nr; ++i)
+      for (int j = 0; j < nt; ++j) et[(size_t)i * nt + j] = -(pst / c.r_lc) * std::sin(g.th(j)) / g.rn(i);
+  }
+  // corotating star and conducting outer wall (Sect. 4)
+  const double omega = 1.0 / c.r_lc;
+  for (int j = 0; j < nt; ++j) {
+    et[j] = -omega * g.rn(0) * std::sin(g.th(j)) * br[j];
+    et[(size_t)nr * nt + j] = 0.0;
+  }
+  const std::vector<double> *F[6] = {&er, &et, &ep, &br, &bt, &bp};
+  for (int k = 0; k < 6; ++k)
+    if ((rc = upload<R>(h, h->o.f[k], *F[k])) != HFF_OK) return rc;
+  if ((rc = upload<R>(h, h->o.f[6], br)) != HFF_OK) return rc;
+  if ((rc = upload<R>(h, h->o.f[7], bt)) != HFF_OK) return rc;
+  if ((rc = upload<R>(h, h->o.f[8], bp)) != HFF_OK) return rc;
+  // injection targets: eligibility f < 1 at the frozen stellar surface
+  // (Sect. 3) and kappa n_GJ V / w with n_GJ = Omega |B_r| / (2 pi e c)
+  std::vector<int32_t> tgt(nt, 0);
+  {
+    double pacc = 0.0;
+    const double r0 = g.rn(0), r1 = g.rn(1);
+    for (int j = 0; j < nt; ++j) {
+      const double p0 = pacc;
+      pacc += br[j] * r0 * r0 * g.dcp(j);
+      const double fs = blend_host(c, unit, 0.5 * (p0 + pacc));
+      if (c.inject && fs < 1.0 && c.w_inj > 0) {
+        const double ngj = omega * std::fabs(br[j]) / (2 * kPi * std::fabs(c.q[0]));
+        const double v = 2.0 * kPi / 3.0 * (r1 * r1 * r1 - r0 * r0 * r0) * g.dcp(j);
+        tgt[j] = (int32_t)std::floor(c.kappa_inj * ngj * v / c.w_inj + 0.5);
+      }
+    }
+  }
+  CK(cudaMemcpyAsync(h->base + h->o.target, tgt.data(), nt * 4, cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+// --------------------------------------------------------- step enqueueing
+template <typename R>
+int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s) {
+  Params<R> &p = params<R>(h)[par];
+  if (stages & HFF_ST_NODE) {
+    launch_psi<R>(p, s);
+    launch_node_a<R>(p, s);
+  }
+  if (stages & HFF_ST_PUSH) {
+    if (h->c.sort_every > 0) {
+      CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
+      launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid);
+    }
+    launch_push_tail<R>(p, s, h->tail_grid);
+  }
+  if (stages & HFF_ST_FARADAY1) launch_faraday<R>(p, R(0.5), false, s);
+  if (stages & HFF_ST_AMPERE) launch_ampere<R>(p, s);
+  if (stages & HFF_ST_CORRECT) launch_correct<R>(p, s);
+  if (stages & HFF_ST_FARADAY2) launch_faraday<R>(p, R(0.5), true, s);
+  if (stages & HFF_ST_INJECT) launch_inject<R>(p, s);
+  else launch_step_done<R>(p, s);
+  CK(cudaGetLastError());
+  return HFF_OK;
+}
+
+template <typename R>
+int enqueue_sort(hff_handle *h, int par, cudaStream_t s) {
+  Params<R> &p = params<R>(h)[par];
+  Params<R> &q = params<R>(h)[par ^ 1];
+  for (int sp = 0; sp < h->c.n_species; ++sp) {
+    launch_sort_species<R>(p, sp, q.sp[sp], h->ss, s);
+    launch_worklist<R>(p, &h->ss, h->wl, sp, sp == 0 ? 1 : 0, s);
+  }
+  CK(cudaGetLastError());
+  return HFF_OK;
+}
+
+int count_kernels(cudaGraph_t g, int64_t *n) {
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  int64_t k = 0;
+  for (auto &x : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(x, &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *n = k;
+  return HFF_OK;
+}
+
+template <typename F>
+int capture(hff_handle *h, F &&fn, cudaGraphExec_t *out, int64_t *nk) {
+  CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+  const int rc = fn(h->cap_st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+  if (rc != HFF_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return fail(HFF_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  int r2 = count_kernels(g, nk);
+  if (r2 != HFF_OK) { cudaGraphDestroy(g); return r2; }
+  const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return fail(HFF_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e2));
+  return HFF_OK;
+}
+
+template <typename R>
+int run_sort_now(hff_handle *h, cudaStream_t s) {
+  int rc = enqueue_sort<R>(h, h->parity, s);
+  if (rc != HFF_OK) return rc;
+  h->parity ^= 1;
+  return HFF_OK;
+}
+
+template <typename R>
+int do_step(hff_handle *h, int32_t n) {
+  for (int32_t k = 0; k < n; ++k) {
+    const int par = h->parity;
+    if (!h->g_step[par]) {
+      int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s); }, &h->g_step[par],
+                       &h->k_step[par]);
+      if (rc != HFF_OK) return rc;
+    }
+    CK(cudaGraphLaunch(h->g_step[par], h->st));
+    h->launched += h->k_step[par];
+    h->step++;
+    if (h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
+      if (!h->g_sort[par]) {
+        int rc = capture(h, [&](cudaStream_t s) { return enqueue_sort<R>(h, par, s); }, &h->g_sort[par],
+                         &h->k_sort[par]);
+        if (rc != HFF_OK) return rc;
+      }
+      CK(cudaGraphLaunch(h->g_sort[par], h->st));
+      h->launched += h->k_sort[par];
+      h->parity ^= 1;
+    }
+  }
+  return HFF_OK;
+}
+
+template <typename R>
+int do_stages(hff_handle *h, int32_t n, int32_t stages) {
+  for (int32_t k = 0; k < n; ++k) {
+    int rc = enqueue_step<R>(h, h->parity, stages, h->st);
+    if (rc != HFF_OK) return rc;
+    h->step++;
+    if ((stages & HFF_ST_SORT) && h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
+      rc = run_sort_now<R>(h, h->st);
+      if (rc != HFF_OK) return rc;
+    }
+  }
+  return HFF_OK;
+}
+
+}  // namespace
+
+// ==================================================================== ABI
+extern "C" {
+
+int hff_plan(const hff_config *cfg, int n_inst, size_t *bytes) {
+  if (n_inst != 1) return fail(HFF_ERR_ARG, "n_inst must be 1");
+  int rc = validate(cfg);
+  if (rc != HFF_OK) return rc;
+  if (!bytes) return fail(HFF_ERR_ARG, "null bytes");
+  Offsets o;
+  layout(*cfg, o);
+  *bytes = o.total;
+  return HFF_OK;
+}
+
+int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, void *stream, hff_handle **out) {
+  if (n_inst != 1) return fail(HFF_ERR_ARG, "n_inst must be 1");
+  int rc = validate(cfg);
+  if (rc != HFF_OK) return rc;
+  if (!dev_mem || !out) return fail(HFF_ERR_ARG, "null pointer");
+  if (((uintptr_t)dev_mem & 255) != 0) return fail(HFF_ERR_ARG, "dev_mem must be 256-byte aligned");
+  hff_handle *h = new hff_handle();
+  h->c = *cfg;
+  h->c.tile_r = tile_r_of(*cfg);
+  h->c.tile_t = tile_t_of(*cfg);
+  layout(h->c, h->o);
+  if (bytes < h->o.total) {
+    delete h;
+    return fail(HFF_ERR_CAPACITY, "dev_mem smaller than hff_plan bytes");
+  }
+  h->st = (cudaStream_t)stream;
+  h->base = (char *)dev_mem;
+  h->g = Geom{cfg->nr, cfg->nt, cfg->r_min, cfg->r_max, std::log(cfg->r_max / cfg->r_min) / cfg->nr,
+              kPi / cfg->nt};
+  h->dt = courant_dt(*cfg);
+  h->psi_unit = psi_unit_of(*cfg);
+  h->xi_abs = std::log(cfg->r_abs / cfg->r_min) / h->g.dlog;
+  h->small = reinterpret_cast<Small *>(h->base + h->o.small);
+  auto bail = [&](int code) { if (h->cap_st) cudaStreamDestroy(h->cap_st); delete h; return code; };
+  if (cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(HFF_ERR_CUDA, "stream create failed"));
+  if (cudaMemsetAsync(h->base, 0, h->o.total, h->st) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "memset failed"));
+  const int parities = cfg->sort_every > 0 ? 2 : 1;
+  for (int p = 0; p < parities; ++p)
+    for (int s = 0; s < cfg->n_species; ++s)
+      if (cfg->capacity > 0 &&
+          cudaMemsetAsync(h->base + h->o.part[p][s][0], 0xFF, (size_t)cfg->capacity * 4, h->st) != cudaSuccess)
+        return bail(fail(HFF_ERR_CUDA, "memset failed"));
+  {
+    const double one = cfg->rr_scale;
+    if (cudaMemcpyAsync(&h->small->rr, &one, sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess)
+      return bail(fail(HFF_ERR_CUDA, "init copy failed"));
+  }
+  // halo of the tiled push: farthest drift between sorts (Courant-bounded)
+  {
+    const double dxi = -std::log(1.0 - h->dt / cfg->r_min) / h->g.dlog;
+    const double deta = std::asin(std::fmin(1.0, h->dt / cfg->r_min)) / h->g.dth;
+    const double d = std::fmax(dxi, deta);
+    h->halo = (int)std::ceil((cfg->sort_every > 0 ? cfg->sort_every : 1) * d + 1e-9);
+  }
+  h->wl.items = reinterpret_cast<int4 *>(h->base + h->o.items);
+  h->wl.n_items = &h->small->n_items;
+  h->wl.next = &h->small->next;
+  h->wl.max_items = h->o.max_items;
+  h->wl.chunk = kChunk;
+  h->ss.keys_a = reinterpret_cast<uint32_t *>(h->base + h->o.keys_a);
+  h->ss.keys_b = reinterpret_cast<uint32_t *>(h->base + h->o.keys_b);
+  h->ss.idx_a = reinterpret_cast<uint32_t *>(h->base + h->o.idx_a);
+  h->ss.idx_b = reinterpret_cast<uint32_t *>(h->base + h->o.idx_b);
+  h->ss.hist = reinterpret_cast<uint32_t *>(h->base + h->o.hist);
+  h->ss.part = reinterpret_cast<uint32_t *>(h->base + h->o.spart);
+  h->ss.tile_start = reinterpret_cast<int *>(h->base + h->o.tstart);
+  h->ss.tile_end = reinterpret_cast<int *>(h->base + h->o.tend);
+  h->ss.cap = cfg->capacity;
+  h->ss.ntiles = h->o.ntiles;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
+  h->tail_grid = nsm * 4;
+  if (cfg->precision == HFF_FP32) {
+    fill_params<float>(h);
+    rc = init_state<float>(h);
+    if (rc == HFF_OK && cfg->sort_every > 0) {
+      const size_t smem = push_tiled_smem<float>(h->pf[0], h->halo);
+      if (smem > 200 * 1024) return bail(fail(HFF_ERR_ARG, "tile + halo too large for shared memory"));
+      if (set_push_smem<float>(smem) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set shared memory size"));
+      int per_sm = (int)((227 * 1024) / (smem + 1024));
+      if (per_sm < 1) per_sm = 1;
+      if (per_sm > 8) per_sm = 8;
+      h->push_grid = nsm * per_sm;
+    }
+  } else {
+    fill_params<double>(h);
+    rc = init_state<double>(h);
+    if (rc == HFF_OK && cfg->sort_every > 0) {
+      const size_t smem = push_tiled_smem<double>(h->pd[0], h->halo);
+      if (smem > 200 * 1024) return bail(fail(HFF_ERR_ARG, "tile + halo too large for shared memory"));
+      if (set_push_smem<double>(smem) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set shared memory size"));
+      int per_sm = (int)((227 * 1024) / (smem + 1024));
+      if (per_sm < 1) per_sm = 1;
+      if (per_sm > 8) per_sm = 8;
+      h->push_grid = nsm * per_sm;
+    }
+  }
+  if (rc != HFF_OK) return bail(rc);
+  *out = h;
+  return HFF_OK;
+}
+
+int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const int32_t *cell, const void *xo,
+                       const void *yo, const void *ur, const void *ut, const void *up, const void *w, int where) {
+  if (!h || inst != 0) return fail(HFF_ERR_ARG, "bad handle or instance");
+  if (species < 0 || species >= h->c.n_species) return fail(HFF_ERR_ARG, "bad species");
+  if (n < 0) return fail(HFF_ERR_ARG, "negative count");
+  if (n > h->c.capacity) return fail(HFF_ERR_CAPACITY, "more particles than capacity");
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  const int pp = (h->c.sort_every > 0) ? h->parity : 0;
+  const cudaMemcpyKind kind = where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const void *src[7] = {cell, xo, yo, ur, ut, up, w};
+  for (int k = 0; k < 7; ++k) {
+    if (n > 0 && !src[k]) return fail(HFF_ERR_ARG, "null particle array");
+    if (n > 0) CK(cudaMemcpyAsync(h->base + h->o.part[pp][species][k], src[k], n * (k == 0 ? 4 : R), kind, h->st));
+  }
+  if (h->c.capacity > n)
+    CK(cudaMemsetAsync(h->base + h->o.part[pp][species][0] + n * 4, 0xFF, (h->c.capacity - n) * 4, h->st));
+  const long long nn = n, zero = 0;
+  CK(cudaMemcpyAsync(&h->small->count[species], &nn, sizeof(nn), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(&h->small->count_sorted[species], &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (h->c.sort_every > 0) {
+    const int rc = h->c.precision == HFF_FP64 ? run_sort_now<double>(h, h->st) : run_sort_now<float>(h, h->st);
+    if (rc != HFF_OK) return rc;
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return HFF_OK;
+}
+
+static int64_t field_elems(const hff_handle *h, int which) {
+  const int64_t nr = h->c.nr, nt = h->c.nt;
+  switch (which) {
+    case 0: case 6: return nr * (nt + 1);
+    case 1: case 7: return (nr + 1) * nt;
+    case 3: return (nr + 1) * nt;
+    case 4: return nr * (nt + 1);
+    case 5: return nr * nt;
+    default: return (nr + 1) * (nt + 1);
+  }
+}
+
+int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where) {
+  if (!h || inst != 0 || which < 0 || which > 5 || !src) return fail(HFF_ERR_ARG, "bad arguments");
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  if (bytes != (size_t)field_elems(h, which) * R) return fail(HFF_ERR_ARG, "byte count does not match the field");
+  CK(cudaMemcpyAsync(h->base + h->o.f[which], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int where) {
+  if (!h || inst != 0 || which < 0 || which > 15 || !dst) return fail(HFF_ERR_ARG, "bad arguments");
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  const size_t want = (size_t)field_elems(h, which) * (which == 9 ? 8 : R);
+  if (bytes != want) return fail(HFF_ERR_ARG, "byte count does not match the field");
+  const cudaMemcpyKind kind = where == HFF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (which == 9) {
+    double *psi = reinterpret_cast<double *>(h->base + h->o.psi64);
+    if (h->c.precision == HFF_FP64) launch_psi64<double>(h->pd[0], psi, h->st);
+    else launch_psi64<float>(h->pf[0], psi, h->st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, psi, bytes, kind, h->st));
+  } else {
+    // offset table order: 0..5 fields, 6..8 initial B, 9..11 J, 12 psi,
+    // 13..15 J_perp, 16..18 Delta E
+    const int slot = which <= 5 ? which : which + 3;
+    CK(cudaMemcpyAsync(dst, h->base + h->o.f[slot], bytes, kind, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+int hff_step(hff_handle *h, int32_t nsteps) {
+  if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  return h->c.precision == HFF_FP64 ? do_step<double>(h, nsteps) : do_step<float>(h, nsteps);
+}
+
+int hff_step_stages(hff_handle *h, int32_t nsteps, int32_t stages) {
+  if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  return h->c.precision == HFF_FP64 ? do_stages<double>(h, nsteps, stages) : do_stages<float>(h, nsteps, stages);
+}
+
+int hff_set_scalar(hff_handle *h, int which, double value) {
+  if (!h || which != HFF_SCALAR_RR_SCALE) return fail(HFF_ERR_ARG, "bad scalar");
+  h->c.rr_scale = value;
+  CK(cudaMemcpyAsync(&h->small->rr, &h->c.rr_scale, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  return HFF_OK;
+}
+
+int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out) {
+  if (!h || inst != 0 || species < 0 || species >= h->c.n_species || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  long long n = 0;
+  CK(cudaMemcpyAsync(&n, &h->small->count[species], sizeof(n), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  const int pp = (h->c.sort_every > 0) ? h->parity : 0;
+  out->n = n;
+  out->cell = reinterpret_cast<int32_t *>(h->base + h->o.part[pp][species][0]);
+  void **q[6] = {&out->xo, &out->yo, &out->ur, &out->ut, &out->up, &out->w};
+  for (int k = 0; k < 6; ++k) *q[k] = h->base + h->o.part[pp][species][k + 1];
+  return HFF_OK;
+}
+
+int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
+  if (!h || inst != 0 || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  const int nr = h->c.nr, nt = h->c.nt;
+  double *q = reinterpret_cast<double *>(h->base + h->o.qnode);
+  double *rows = reinterpret_cast<double *>(h->base + h->o.rows);
+  double *psi = reinterpret_cast<double *>(h->base + h->o.psi64);
+  if (h->c.precision == HFF_FP64) {
+    launch_diag<double>(h->pd[h->c.sort_every > 0 ? h->parity : 0], h->dg, q, h->small->kin, h->small->cnt, rows, h->st);
+    launch_psi64<double>(h->pd[0], psi, h->st);
+  } else {
+    launch_diag<float>(h->pf[h->c.sort_every > 0 ? h->parity : 0], h->dg, q, h->small->kin, h->small->cnt, rows, h->st);
+    launch_psi64<float>(h->pf[0], psi, h->st);
+  }
+  CK(cudaGetLastError());
+  std::vector<double> hr((size_t)(nr + 1) * 8);
+  Small sm;
+  CK(cudaMemcpyAsync(hr.data(), rows, hr.size() * 8, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&sm, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  int iout = (int)std::floor(std::log(2.0 * h->c.r_lc / h->c.r_min) / h->g.dlog + 0.5);
+  if (iout > nr) iout = nr;
+  double po = 0;
+  CK(cudaMemcpyAsync(&po, psi + (size_t)iout * (nt + 1) + nt / 2, 8, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::memset(out, 0, sizeof(*out));
+  out->psi_open = po;
+  double sin_ = 0, sout = 0, ue = 0, ub = 0, g2 = 0, gc = 0, gmax = 0, rmax = 0;
+  int nin = 0, nout = 0;
+  for (int i = 0; i <= nr; ++i) {
+    const double *o = &hr[(size_t)i * 8];
+    if (i < nr) {
+      if (l_prof) l_prof[i] = o[0];
+      const double r = h->g.rh(i);
+      if (r >= h->c.r_min && r <= 2 * h->c.r_min) { sin_ += o[0]; nin++; }
+      if (r >= 2 * h->c.r_lc && r <= 3 * h->c.r_lc) { sout += o[0]; nout++; }
+    }
+    ue += o[1]; ub += o[2]; gmax = std::fmax(gmax, o[3]); g2 += o[4]; gc += o[5]; rmax = std::fmax(rmax, o[6]);
+  }
+  out->l_in = nin ? sin_ / nin : 0;
+  out->l_out = nout ? sout / nout : 0;
+  out->eps = out->l_out != 0 ? std::fabs(out->l_in - out->l_out) / std::fabs(out->l_out) : 0;
+  out->gauss_max = gmax;
+  out->gauss_rms = gc > 0 ? std::sqrt(g2 / gc) : 0;
+  out->rho_max = rmax;
+  out->u_e = ue / (8 * kPi);
+  out->u_b = ub / (8 * kPi);
+  for (int s = 0; s < kMaxSpecies; ++s) { out->kinetic[s] = sm.kin[s]; out->count[s] = sm.cnt[s]; }
+  out->injected = sm.acc[0];
+  out->killed = sm.acc[1];
+  out->radiated = sm.acc[2];
+  out->nonfinite = sm.acc[3];
+  return HFF_OK;
+}
+
+int hff_get_info(hff_handle *h, hff_info *out) {
+  if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  Small sm;
+  CK(cudaMemcpyAsync(&sm, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  std::memset(out, 0, sizeof(*out));
+  out->dt = h->dt;
+  out->psi_unit = h->psi_unit;
+  out->step = h->step;
+  for (int s = 0; s < kMaxSpecies; ++s) out->count[s] = sm.count[s];
+  out->tile_r = h->c.tile_r;
+  out->tile_t = h->c.tile_t;
+  out->sort_every = h->c.sort_every;
+  out->precision = h->c.precision;
+  out->kernels_per_step = h->k_step[0] ? h->k_step[0] : h->k_step[1];
+  out->kernels_launched = h->launched;
+  return HFF_OK;
+}
+
+int hff_status(hff_handle *h) {
+  if (!h) return fail(HFF_ERR_ARG, "null handle");
+  unsigned st = 0, zero = 0;
+  CK(cudaMemcpyAsync(&st, &h->small->status, sizeof(st), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&h->small->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (st & kStCapacity) return fail(HFF_ERR_CAPACITY, "particle capacity exceeded on the device");
+  if (st & kStWorklist) return fail(HFF_ERR_CAPACITY, "work list overflow");
+  if (st & kStNonfinite) return fail(HFF_ERR_NONFINITE, "non-finite particle state removed");
+  return HFF_OK;
+}
+
+int hff_destroy(hff_handle *h) {
+  if (!h) return fail(HFF_ERR_ARG, "null handle");
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (int p = 0; p < 2; ++p) {
+    if (h->g_step[p]) cudaGraphExecDestroy(h->g_step[p]);
+    if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
+  }
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  delete h;
+  return HFF_OK;
+}
+
+const char *hff_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// fields.cu -- grid kernels of the hybrid step: flux function (Eq. 27),
+// force-free perpendicular current (Eq. 24, first term), Yee advance in
+// Stokes form (Eqs. 18-19) with the blended current (Eq. 28), the E
+// renormalisation (Eqs. 25-26), the corotating star and the absorber.
+//
+// Mapping: theta is the fastest index of every array, so a warp walks 32
+// consecutive theta points of one r row (coalesced); blockIdx.y is the row.
+// All these kernels are HBM-bound stencils: each reads its inputs once per
+// step through L1/L2 (neighbour reuse hits cache) and writes its outputs once.
+#include "hff_common.cuh"
+
+namespace hff {
+
+constexpr int kRowThreads = 128;
+
+// ------------------------------------------------------------ Psi (Eq. 27)
+// Psi(i, 0) = 0, Psi(i, j+1) = Psi(i, j) + B_r(i, j+1/2) r_i^2 dcp_j, an
+// inclusive prefix along theta accumulated in FP64.  One block per r row.
+template <typename R>
+__global__ void __launch_bounds__(256) k_psi(Params<R> p) {
+  const int i = blockIdx.x;
+  const int nt = p.nt;
+  const R *br = p.f.br + (int64_t)i * nt;
+  R *psi = p.f.psi + (int64_t)i * (nt + 1);
+  const double r2 = p.t.r2n[i];
+  __shared__ double warp_tot[8];
+  __shared__ double carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry = 0.0; psi[0] = R(0); }
+  __syncthreads();
+  for (int seg = 0; seg < nt; seg += 256) {
+    const int j = seg + threadIdx.x;
+    double v = (j < nt) ? (double)br[j] * p.t.dcp[j] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    double off = carry;
+    for (int w = 0; w < wid; ++w) off += warp_tot[w];
+    if (j < nt) psi[j + 1] = (R)(r2 * (off + v));
+    __syncthreads();
+    if (threadIdx.x == 255) carry = off + v;
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------- collocation
+// Arithmetic means of the staggered neighbours at node (i, j) (Sect. 3);
+// interior rows only; transverse components vanish on the axis.
+template <typename R>
+__device__ __forceinline__ void collocate(const Params<R> &p, int i, int j, R e[3], R b[3]) {
+  const int nt = p.nt, n1 = nt + 1;
+  const bool axis = (j == 0 || j == nt);
+  const Fields<R> &f = p.f;
+  e[0] = R(0.5) * (f.er[ix(i - 1, j, n1)] + f.er[ix(i, j, n1)]);
+  e[1] = axis ? R(0) : R(0.5) * (f.et[ix(i, j - 1, nt)] + f.et[ix(i, j, nt)]);
+  e[2] = axis ? R(0) : f.ep[ix(i, j, n1)];
+  b[0] = (j == 0) ? f.br[ix(i, 0, nt)]
+                  : (j == nt) ? f.br[ix(i, nt - 1, nt)]
+                              : R(0.5) * (f.br[ix(i, j - 1, nt)] + f.br[ix(i, j, nt)]);
+  b[1] = axis ? R(0) : R(0.5) * (f.bt[ix(i - 1, j, n1)] + f.bt[ix(i, j, n1)]);
+  b[2] = axis ? R(0)
+              : R(0.25) * (f.bp[ix(i - 1, j - 1, nt)] + f.bp[ix(i - 1, j, nt)] +
+                           f.bp[ix(i, j - 1, nt)] + f.bp[ix(i, j, nt)]);
+}
+
+template <typename R> __device__ __forceinline__ R b2min();
+template <> __device__ __forceinline__ float b2min<float>() { return 1e-30f; }
+template <> __device__ __forceinline__ double b2min<double>() { return 1e-30; }
+
+// ----------------------------------------------------------- node pass A
+// rho = div E / 4 pi over the node dual cell and J_perp = c rho E x B / B^2
+// (first term of Eq. 24) from E^n, B^n; plus the per-cell pure force-free
+// flag f(Psi_cell) >= 1 used to remove particles (Eq. 29: no particles).
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_node_a(Params<R> p) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  const Fields<R> &f = p.f;
+  if (i < nr && j < nt) {
+    const R pc = R(0.25) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)] + f.psi[ix(i, j + 1, n1)] +
+                            f.psi[ix(i + 1, j + 1, n1)]);
+    f.ffcell[ix(i, j, nt)] = (blend(p, pc) >= R(1)) ? 1 : 0;
+  }
+  R jx = 0, jy = 0, jz = 0;
+  if (i >= 1 && i < nr) {
+    R e[3], b[3];
+    collocate(p, i, j, e, b);
+    R div = p.t.rho_a[i] * (p.t.rh2[i] * f.er[ix(i, j, n1)] - p.t.rh2[i - 1] * f.er[ix(i - 1, j, n1)]);
+    R dt = 0;
+    if (j < nt) dt += p.t.sh[j] * f.et[ix(i, j, nt)];
+    if (j > 0) dt -= p.t.sh[j - 1] * f.et[ix(i, j - 1, nt)];
+    const R rho = div + p.t.rho_b[i] * dt * p.t.inv_dch[j];
+    const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    if (b2 > b2min<R>()) {
+      const R s = rho / b2;
+      jx = s * (e[1] * b[2] - e[2] * b[1]);
+      jy = s * (e[2] * b[0] - e[0] * b[2]);
+      jz = s * (e[0] * b[1] - e[1] * b[0]);
+    }
+  }
+  f.jpr[ix(i, j, n1)] = jx;
+  f.jpt[ix(i, j, n1)] = jy;
+  f.jpp[ix(i, j, n1)] = jz;
+}
+
+// ---------------------------------------------------------------- Faraday
+// Eq. 18 over the exact primary faces, B -= h dt curl E; optionally the
+// absorber B -= sigma (B - B_0) afterwards.
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_faraday(Params<R> p, R hdt, bool absorb) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  const Fields<R> &f = p.f;
+  const Tables<R> &t = p.t;
+  if (j < nt) {  // B_r(i, j+1/2), i = 0..nr
+    const R c = t.inv_rn[i] * (t.sn[j + 1] * f.ep[ix(i, j + 1, n1)] - t.sn[j] * f.ep[ix(i, j, n1)]) *
+                t.inv_dcp[j];
+    R v = f.br[ix(i, j, nt)] - hdt * c;
+    if (absorb) { const R sg = t.sig_n[i]; if (sg > R(0)) v -= sg * (v - f.br0[ix(i, j, nt)]); }
+    f.br[ix(i, j, nt)] = v;
+  }
+  if (i < nr) {
+    // B_th(i+1/2, j): zero on the axis
+    R v = R(0);
+    if (j > 0 && j < nt) {
+      v = f.bt[ix(i, j, n1)] +
+          hdt * t.c_b2[i] * (t.rn[i + 1] * f.ep[ix(i + 1, j, n1)] - t.rn[i] * f.ep[ix(i, j, n1)]);
+      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) v -= sg * (v - f.bt0[ix(i, j, n1)]); }
+    }
+    f.bt[ix(i, j, n1)] = v;
+    if (j < nt) {  // B_ph(i+1/2, j+1/2)
+      const R c = t.c_b2[i] * (t.rn[i + 1] * f.et[ix(i + 1, j, nt)] - t.rn[i] * f.et[ix(i, j, nt)]) -
+                  t.c_bp2[i] * (f.er[ix(i, j + 1, n1)] - f.er[ix(i, j, n1)]);
+      R w = f.bp[ix(i, j, nt)] - hdt * c;
+      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) w -= sg * (w - f.bp0[ix(i, j, nt)]); }
+      f.bp[ix(i, j, nt)] = w;
+    }
+  }
+}
+
+// mean of a node quantity over the two nodes of a radial edge (interior
+// nodes only: rows 0 and nr carry the boundary conditions)
+template <typename R>
+__device__ __forceinline__ R edge_r_mean(const R *a, int i, int j, int nr, int n1) {
+  const bool lo = i >= 1, hi = i + 1 <= nr - 1;
+  R v = R(0);
+  if (lo) v += a[ix(i, j, n1)];
+  if (hi) v += a[ix(i + 1, j, n1)];
+  return (lo && hi) ? R(0.5) * v : v;
+}
+
+// ---------------------------------------------------------------- Ampere
+// Eq. 19 over the exact dual faces with J = (1 - f) J_PIC + f J_FFE (Eq. 28);
+// then the corotating star (tangential E fixed, Sect. 4), the conducting
+// outer wall, E_ph = 0 on the axis, the absorber on E, and J_PIC cleared.
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  const Fields<R> &f = p.f;
+  const Tables<R> &t = p.t;
+  const R dt = p.dt, fp = R(4.0 * kPi) * p.dt;
+  if (i < nr) {  // E_r(i+1/2, j)
+    R c = R(0);
+    if (j < nt) c += t.sh[j] * f.bp[ix(i, j, nt)];
+    if (j > 0) c -= t.sh[j - 1] * f.bp[ix(i, j - 1, nt)];
+    c *= t.inv_rh[i] * t.inv_dch[j];
+    const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
+    const int64_t k = ix(i, j, n1);
+    const R jt = (R(1) - fb) * f.jr[k] + fb * edge_r_mean(f.jpr, i, j, nr, n1);
+    f.er[k] = (f.er[k] + dt * c - fp * jt) * (R(1) - t.sig_h[i]);
+    f.jr[k] = R(0);
+  }
+  if (j < nt) {  // E_th(i, j+1/2)
+    const int64_t k = ix(i, j, nt);
+    R v;
+    if (i == 0) {
+      v = -p.omega * t.rn[0] * t.sh[j] * f.br[ix(0, j, nt)];
+    } else if (i == nr) {
+      v = R(0);
+    } else {
+      const R c = -t.c_e2[i] * (t.rh[i] * f.bp[ix(i, j, nt)] - t.rh[i - 1] * f.bp[ix(i - 1, j, nt)]);
+      const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
+      const R jt = (R(1) - fb) * f.jt[k] + fb * R(0.5) * (f.jpt[ix(i, j, n1)] + f.jpt[ix(i, j + 1, n1)]);
+      v = (f.et[k] + dt * c - fp * jt) * (R(1) - t.sig_n[i]);
+    }
+    f.et[k] = v;
+    f.jt[k] = R(0);
+  }
+  {  // E_ph(i, j)
+    const int64_t k = ix(i, j, n1);
+    R v = R(0);
+    if (i >= 1 && i < nr && j >= 1 && j < nt) {
+      const R c = t.c_e2[i] * (t.rh[i] * f.bt[ix(i, j, n1)] - t.rh[i - 1] * f.bt[ix(i - 1, j, n1)]) -
+                  t.c_ep2[i] * (f.br[ix(i, j, nt)] - f.br[ix(i, j - 1, nt)]);
+      const R fb = blend(p, f.psi[k]);
+      const R jt = (R(1) - fb) * f.jp[k] + fb * f.jpp[k];
+      v = (f.ep[k] + dt * c - fp * jt) * (R(1) - t.sig_n[i]);
+    }
+    f.ep[k] = v;
+    f.jp[k] = R(0);
+  }
+}
+
+// ----------------------------------------------------------- node pass B
+// Renormalisation at interior nodes from E^{n+1} and B^{n+1/2}:
+// E' = E - (E.B) B/B^2 (Eq. 25), E'' = sqrt(B^2/E'^2) E' if E'^2 > B^2 (Eq. 26).
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  R d0 = 0, d1 = 0, d2 = 0;
+  if (i >= 1 && i < nr) {
+    R e[3], b[3];
+    collocate(p, i, j, e, b);
+    const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    if (b2 > b2min<R>()) {
+      const R s = (e[0] * b[0] + e[1] * b[1] + e[2] * b[2]) / b2;
+      const R x = e[0] - s * b[0], y = e[1] - s * b[1], z = e[2] - s * b[2];
+      const R e2 = x * x + y * y + z * z;
+      const R sc = (e2 > b2) ? sqrt(b2 / e2) : R(1);
+      d0 = sc * x - e[0];
+      d1 = sc * y - e[1];
+      d2 = sc * z - e[2];
+    }
+  }
+  p.f.der[ix(i, j, n1)] = d0;
+  p.f.det[ix(i, j, n1)] = d1;
+  p.f.dep[ix(i, j, n1)] = d2;
+}
+
+// Delta E interpolated back to the staggered mesh by arithmetic means and
+// applied with the blend weight f (Sect. 3, Eqs. 29-31).
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  const Fields<R> &f = p.f;
+  if (i < nr) {
+    const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
+    if (fb != R(0)) f.er[ix(i, j, n1)] += fb * edge_r_mean(f.der, i, j, nr, n1);
+  }
+  if (i >= 1 && i < nr) {
+    if (j < nt) {
+      const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
+      if (fb != R(0)) f.et[ix(i, j, nt)] += fb * R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]);
+    }
+    if (j >= 1 && j < nt) {
+      const R fb = blend(p, f.psi[ix(i, j, n1)]);
+      if (fb != R(0)) f.ep[ix(i, j, n1)] += fb * f.dep[ix(i, j, n1)];
+    }
+  }
+}
+
+// corotating star and zero tangential E at the outer wall and E_ph on the axis
+template <typename R>
+__global__ void k_bc(Params<R> p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j < nt) {
+    p.f.et[ix(0, j, nt)] = -p.omega * p.t.rn[0] * p.t.sh[j] * p.f.br[ix(0, j, nt)];
+    p.f.et[ix(nr, j, nt)] = R(0);
+  }
+  if (j <= nt) { p.f.ep[ix(0, j, n1)] = R(0); p.f.ep[ix(nr, j, n1)] = R(0); }
+  for (int i = j; i <= nr; i += gridDim.x * blockDim.x) {
+    p.f.ep[ix(i, 0, n1)] = R(0);
+    p.f.ep[ix(i, nt, n1)] = R(0);
+  }
+}
+
+static inline dim3 row_grid(int rows, int nt) { return dim3((nt + 1 + kRowThreads - 1) / kRowThreads, rows); }
+
+template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s) {
+  k_psi<R><<<p.nr + 1, 256, 0, s>>>(p);
+}
+template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s) {
+  k_node_a<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+}
+template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s) {
+  k_faraday<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p, half * p.dt, absorb);
+}
+template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s) {
+  k_ampere<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+}
+template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s) {
+  k_node_b<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+  k_correct<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+}
+template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s) {
+  const int n = (p.nr > p.nt ? p.nr : p.nt) + 2;
+  k_bc<R><<<(n + 255) / 256, 256, 0, s>>>(p);
+}
+
+#define HFF_INST(R)                                                            \
+  template void launch_psi<R>(const Params<R> &, cudaStream_t);                \
+  template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
+  template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
+  template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
+  template void launch_correct<R>(const Params<R> &, cudaStream_t);            \
+  template void launch_bc<R>(const Params<R> &, cudaStream_t);
+HFF_INST(float)
+HFF_INST(double)
+#undef HFF_INST
+
+}  // namespace hff

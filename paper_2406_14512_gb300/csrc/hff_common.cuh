@@ -1,0 +1,156 @@
+// hff_common.cuh -- device-side data layout shared by the kernels of the
+// hybrid force-free / PIC step.  All geometry is precomputed on the host in
+// FP64 from the exact-integral definitions (lengths, areas and volumes of the
+// log-spherical Yee mesh) and stored as separable row (r) and column (theta)
+// factors in the working precision R.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hff {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxBreaks = 4;
+constexpr double kPi = 3.14159265358979323846;
+
+// status bits latched on the device
+constexpr unsigned kStCapacity = 1u;
+constexpr unsigned kStNonfinite = 2u;
+constexpr unsigned kStWorklist = 4u;
+
+template <typename R>
+struct Tables {
+  // rows
+  const R *rn;      // nr+1  r_i
+  const R *inv_rn;  // nr+1  1/r_i
+  const R *rh;      // nr    r_{i+1/2}
+  const R *inv_rh;  // nr    1/r_{i+1/2}
+  const R *c_b2;    // nr    2/(r_{i+1}^2 - r_i^2)
+  const R *c_bp2;   // nr    2 (r_{i+1} - r_i)/((r_{i+1}^2 - r_i^2) dtheta)
+  const R *c_e2;    // nr+1  2/(rhi^2 - rlo^2) of the node dual cell
+  const R *c_ep2;   // nr+1  2 (rhi - rlo)/((rhi^2 - rlo^2) dtheta)
+  const R *rho_a;   // nr+1  3/(4 pi (rhi^3 - rlo^3))
+  const R *rho_b;   // nr+1  3 (rhi^2 - rlo^2)/(8 pi (rhi^3 - rlo^3))
+  const R *rh2;     // nr    r_{i+1/2}^2
+  const R *dep_r;   // nr    1/(2 pi r_{i+1/2}^2 dt)
+  const R *dep_t;   // nr+1  1/(pi (rhi^2 - rlo^2) dt)
+  const R *dep_p;   // nr+1  3/(2 pi (rhi^3 - rlo^3))
+  const R *sig_n;   // nr+1  absorber damping at r_i
+  const R *sig_h;   // nr    absorber damping at r_{i+1/2}
+  const double *r2n;  // nr+1  r_i^2 (Psi prefix, FP64)
+  // columns
+  const R *sn;      // nt+1  sin theta_j
+  const R *sh;      // nt    sin theta_{j+1/2}
+  const R *inv_sh;  // nt    1/sin theta_{j+1/2}
+  const R *inv_dcp; // nt    1/(cos theta_j - cos theta_{j+1})
+  const R *inv_dch; // nt+1  1/(cos theta_lo - cos theta_hi) of the node dual cell
+  const double *dcp;  // nt    cos theta_j - cos theta_{j+1} (Psi prefix, FP64)
+};
+
+template <typename R>
+struct Fields {
+  R *er, *et, *ep, *br, *bt, *bp;   // E^n, B^n (B^{n+1/2} between the half steps)
+  R *br0, *bt0, *bp0;               // initial B (absorber reference)
+  R *jr, *jt, *jp;                  // J_PIC accumulators (E locations)
+  R *psi;                           // Psi at nodes (FP64 prefix, rounded to R)
+  R *jpr, *jpt, *jpp;               // J_perp at nodes
+  R *der, *det, *dep;               // Delta E at nodes
+  uint8_t *ffcell;                  // 1 = cell in the pure force-free domain
+};
+
+template <typename R>
+struct Species {
+  int32_t *cell;
+  R *xo, *yo, *ur, *ut, *up, *w;
+};
+
+template <typename R>
+struct Params {
+  int nr, nt;
+  R dt, dlog, dth, omega, r_min, xi_abs, shell_r2;
+  int n_breaks;
+  R psi_break[kMaxBreaks];  // absolute units
+  R f_break[kMaxBreaks];
+  int n_species;
+  R q[kMaxSpecies], qm[kMaxSpecies], m[kMaxSpecies], krr[kMaxSpecies];
+  Tables<R> t;
+  Fields<R> f;
+  Species<R> sp[kMaxSpecies];
+  int64_t cap;
+  long long *count;         // [kMaxSpecies] slots in use (device)
+  long long *count_sorted;  // [kMaxSpecies] length of the tile-sorted prefix
+  const double *rr_scale;   // device scalar (ramp)
+  int32_t *surf;            // [nt] live particles per surface cell after the move
+  const int32_t *target;    // [nt] injection targets (fixed at init)
+  int32_t *inj_prefix;      // [nt+1]
+  long long *inj_base;      // [kMaxSpecies] slot of the first injected particle
+  long long *step;          // device step counter (injection key)
+  uint32_t seed_lo, seed_hi;
+  int inject;
+  R w_inj;
+  double *acc;              // [4] injected, killed, radiated, nonfinite
+  unsigned *status;
+  int tile_r, tile_t, ntt;  // sort tiles
+};
+
+// piecewise-linear blend f(Psi) of Eqs. 29-31 (right-continuous at jumps)
+template <typename R>
+__device__ __forceinline__ R blend(const Params<R> &p, R psi) {
+  const int n = p.n_breaks;
+  if (n <= 0) return R(0);
+  if (psi < p.psi_break[0]) return p.f_break[0];
+#pragma unroll
+  for (int k = 1; k < kMaxBreaks; ++k) {
+    if (k < n && psi < p.psi_break[k]) {
+      const R x0 = p.psi_break[k - 1], x1 = p.psi_break[k];
+      return p.f_break[k - 1] + (p.f_break[k] - p.f_break[k - 1]) * (psi - x0) / (x1 - x0);
+    }
+  }
+  return p.f_break[n - 1];
+}
+
+// row-major helpers (theta fastest)
+__device__ __forceinline__ int64_t ix(int i, int j, int ld) { return (int64_t)i * ld + j; }
+
+// launchers (defined in fields.cu / particles.cu / sort.cu / diag.cu)
+template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s);
+template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s);
+template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s);
+template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);
+template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
+template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s);
+
+struct WorkList {
+  int4 *items;          // (species, tile, start, count)
+  int *n_items;         // device count
+  int *next;            // dynamic scheduling counter
+  int max_items;
+  int chunk;            // particles per item
+};
+
+template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, int grid);
+template <typename R> void launch_push_tiled(const Params<R> &p, const WorkList &wl, int halo,
+                                             cudaStream_t s, int grid);
+template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo);
+template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s);
+template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s);
+template <typename R> cudaError_t set_push_smem(size_t bytes);
+
+struct SortScratch {
+  uint32_t *keys_a, *keys_b;   // cap
+  uint32_t *idx_a, *idx_b;     // cap
+  uint32_t *hist;              // 256 * max_blocks
+  uint32_t *part;              // block sums of the scan
+  int *tile_start;             // [ntiles + 1] first sorted slot of each tile
+  int *tile_end;               // [ntiles + 1] one past its last slot
+  int64_t cap;
+  int ntiles;
+};
+
+template <typename R> void launch_sort_species(const Params<R> &p, int species, Species<R> dst,
+                                               const SortScratch &ss, cudaStream_t s);
+template <typename R> void launch_worklist(const Params<R> &p, const SortScratch *ss,
+                                           const WorkList &wl, int species, int first,
+                                           cudaStream_t s);
+
+}  // namespace hff

@@ -1,0 +1,546 @@
+// particles.cu -- particle side of the hybrid step: linear gather from the
+// staggered mesh, modified Boris push with radiation reaction (Eqs. 15-17),
+// removal of u_perp near the star (Sect. 5.1), straight-line move in the
+// local Cartesian frame, charge-conserving (Esirkepov) deposit of J_PIC, and
+// the surface pair injection (Sects. 4 and 5.1).
+//
+// Two drivers share one per-particle routine:
+//  * k_push_tiled -- persistent blocks take (species, tile, chunk) work items
+//    from a list built by the sort.  The block stages E, B and the force-free
+//    flags of the tile plus a halo (the farthest a particle can drift between
+//    sorts) into shared memory, accumulates J in shared memory with shared
+//    atomics, and flushes the tile's J with one global atomic per nonzero
+//    entry.  Particles of a tile are contiguous, so the particle stream is
+//    read and written once, fully coalesced.
+//  * k_push_tail -- particles appended since the last sort (injection) and
+//    the no-sort configuration: gathers through L1/L2 and global atomics.
+#include "hff_common.cuh"
+
+namespace hff {
+
+// -------------------------------------------------------------- accessors
+// Global-memory view of the mesh.
+template <typename R>
+struct GlobalMesh {
+  const Params<R> &p;
+  __device__ GlobalMesh(const Params<R> &pp) : p(pp) {}
+  __device__ __forceinline__ R er(int i, int j) const { return p.f.er[ix(i, j, p.nt + 1)]; }
+  __device__ __forceinline__ R et(int i, int j) const { return p.f.et[ix(i, j, p.nt)]; }
+  __device__ __forceinline__ R ep(int i, int j) const { return p.f.ep[ix(i, j, p.nt + 1)]; }
+  __device__ __forceinline__ R br(int i, int j) const { return p.f.br[ix(i, j, p.nt)]; }
+  __device__ __forceinline__ R bt(int i, int j) const { return p.f.bt[ix(i, j, p.nt + 1)]; }
+  __device__ __forceinline__ R bp(int i, int j) const { return p.f.bp[ix(i, j, p.nt)]; }
+  __device__ __forceinline__ bool ff(int i, int j) const { return p.f.ffcell[ix(i, j, p.nt)] != 0; }
+  __device__ __forceinline__ void add_jr(int i, int j, R v) const { atomicAdd(&p.f.jr[ix(i, j, p.nt + 1)], v); }
+  __device__ __forceinline__ void add_jt(int i, int j, R v) const { atomicAdd(&p.f.jt[ix(i, j, p.nt)], v); }
+  __device__ __forceinline__ void add_jp(int i, int j, R v) const { atomicAdd(&p.f.jp[ix(i, j, p.nt + 1)], v); }
+};
+
+// Shared-memory view of a tile region [i0, i0 + LR) x [j0, j0 + LT) of every
+// component (indices are global; the caller guarantees they fall inside).
+template <typename R>
+struct SharedMesh {
+  R *s_er, *s_et, *s_ep, *s_br, *s_bt, *s_bp, *s_jr, *s_jt, *s_jp;
+  uint8_t *s_ff;
+  int i0, j0, lt;
+  __device__ __forceinline__ int o(int i, int j) const { return (i - i0) * lt + (j - j0); }
+  __device__ __forceinline__ R er(int i, int j) const { return s_er[o(i, j)]; }
+  __device__ __forceinline__ R et(int i, int j) const { return s_et[o(i, j)]; }
+  __device__ __forceinline__ R ep(int i, int j) const { return s_ep[o(i, j)]; }
+  __device__ __forceinline__ R br(int i, int j) const { return s_br[o(i, j)]; }
+  __device__ __forceinline__ R bt(int i, int j) const { return s_bt[o(i, j)]; }
+  __device__ __forceinline__ R bp(int i, int j) const { return s_bp[o(i, j)]; }
+  __device__ __forceinline__ bool ff(int i, int j) const { return s_ff[o(i, j)] != 0; }
+  __device__ __forceinline__ void add_jr(int i, int j, R v) const { atomicAdd(&s_jr[o(i, j)], v); }
+  __device__ __forceinline__ void add_jt(int i, int j, R v) const { atomicAdd(&s_jt[o(i, j)], v); }
+  __device__ __forceinline__ void add_jp(int i, int j, R v) const { atomicAdd(&s_jp[o(i, j)], v); }
+};
+
+// 1D linear weights for a component at positions k + a (a = 0 or 1/2),
+// k = 0 .. n-1, constant beyond the ends.
+template <typename R>
+__device__ __forceinline__ void stag(int c, R o, bool half, int n, int &k0, R &w) {
+  if (!half) { k0 = c; w = o; }
+  else if (o >= R(0.5)) { k0 = c; w = o - R(0.5); }
+  else { k0 = c - 1; w = o + R(0.5); }
+  if (k0 < 0) { k0 = 0; w = R(0); }
+  if (k0 > n - 2) { k0 = n - 2; w = R(1); }
+}
+
+template <typename R, typename M, typename Get>
+__device__ __forceinline__ R interp(const M &m, Get g, int i, R wi, int j, R wj) {
+  return (R(1) - wi) * ((R(1) - wj) * g(m, i, j) + wj * g(m, i, j + 1)) +
+         wi * ((R(1) - wj) * g(m, i + 1, j) + wj * g(m, i + 1, j + 1));
+}
+
+template <typename R, typename M>
+__device__ __forceinline__ void gather(const M &m, int nr, int nt, int i, int j, R xo, R yo, R e[3], R b[3]) {
+  int ki, kj;
+  R wi, wj;
+  stag(i, xo, true, nr, ki, wi); stag(j, yo, false, nt + 1, kj, wj);
+  e[0] = interp(m, [](const M &q, int a, int c) { return q.er(a, c); }, ki, wi, kj, wj);
+  b[1] = interp(m, [](const M &q, int a, int c) { return q.bt(a, c); }, ki, wi, kj, wj);
+  stag(i, xo, false, nr + 1, ki, wi); stag(j, yo, true, nt, kj, wj);
+  e[1] = interp(m, [](const M &q, int a, int c) { return q.et(a, c); }, ki, wi, kj, wj);
+  b[0] = interp(m, [](const M &q, int a, int c) { return q.br(a, c); }, ki, wi, kj, wj);
+  stag(i, xo, false, nr + 1, ki, wi); stag(j, yo, false, nt + 1, kj, wj);
+  e[2] = interp(m, [](const M &q, int a, int c) { return q.ep(a, c); }, ki, wi, kj, wj);
+  stag(i, xo, true, nr, ki, wi); stag(j, yo, true, nt, kj, wj);
+  b[2] = interp(m, [](const M &q, int a, int c) { return q.bp(a, c); }, ki, wi, kj, wj);
+}
+
+// Modified Boris step (Eqs. 15-17, c = 1): Lorentz Boris gives u_L, the
+// radiation-reaction kick K F_RR is evaluated at the time-centred momentum
+// (u + u_L)/2 and limited to half of |u_L| per step.  Bperp^2 of Eq. 17 is
+// evaluated as |F x beta|^2 + |F|^2 / gamma^2 with F = E + beta x B, which
+// equals |F|^2 - (beta.F)^2 = |F|^2 - (beta.E)^2 without cancellation.
+template <typename R>
+__device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const R e[3], const R b[3],
+                                         R out[3], R &dgam) {
+  const R a = R(0.5) * qm * dt;
+  const R um0 = u[0] + a * e[0], um1 = u[1] + a * e[1], um2 = u[2] + a * e[2];
+  const R ig = R(1) / sqrt(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
+  const R t0 = a * b[0] * ig, t1 = a * b[1] * ig, t2 = a * b[2] * ig;
+  const R sc = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
+  const R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;
+  const R v0 = um0 + (um1 * t2 - um2 * t1), v1 = um1 + (um2 * t0 - um0 * t2), v2 = um2 + (um0 * t1 - um1 * t0);
+  const R ul0 = um0 + (v1 * s2 - v2 * s1) + a * e[0];
+  const R ul1 = um1 + (v2 * s0 - v0 * s2) + a * e[1];
+  const R ul2 = um2 + (v0 * s1 - v1 * s0) + a * e[2];
+  out[0] = ul0; out[1] = ul1; out[2] = ul2;
+  dgam = R(0);
+  if (krr != R(0)) {
+    const R ub0 = R(0.5) * (u[0] + ul0), ub1 = R(0.5) * (u[1] + ul1), ub2 = R(0.5) * (u[2] + ul2);
+    const R g2 = R(1) + ub0 * ub0 + ub1 * ub1 + ub2 * ub2;
+    const R ig2 = R(1) / sqrt(g2);
+    const R be0 = ub0 * ig2, be1 = ub1 * ig2, be2 = ub2 * ig2;
+    const R f0 = e[0] + (be1 * b[2] - be2 * b[1]);
+    const R f1 = e[1] + (be2 * b[0] - be0 * b[2]);
+    const R f2 = e[2] + (be0 * b[1] - be1 * b[0]);
+    const R c0 = f1 * be2 - f2 * be1, c1 = f2 * be0 - f0 * be2, c2 = f0 * be1 - f1 * be0;
+    const R ff = f0 * f0 + f1 * f1 + f2 * f2;
+    const R bp2 = c0 * c0 + c1 * c1 + c2 * c2 + ff / g2;
+    const R bdot = be0 * e[0] + be1 * e[1] + be2 * e[2];
+    const R k = dt * krr;
+    const R du0 = k * ((f1 * b[2] - f2 * b[1]) + bdot * e[0] - g2 * bp2 * be0);
+    const R du1 = k * ((f2 * b[0] - f0 * b[2]) + bdot * e[1] - g2 * bp2 * be1);
+    const R du2 = k * ((f0 * b[1] - f1 * b[0]) + bdot * e[2] - g2 * bp2 * be2);
+    const R dn2 = du0 * du0 + du1 * du1 + du2 * du2, ul2s = ul0 * ul0 + ul1 * ul1 + ul2 * ul2;
+    const R lim = (dn2 > R(0.25) * ul2s) ? R(0.5) * sqrt(ul2s / dn2) : R(1);
+    out[0] = ul0 + lim * du0;
+    out[1] = ul1 + lim * du1;
+    out[2] = ul2 + lim * du2;
+    dgam = sqrt(R(1) + ul2s) - sqrt(R(1) + out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+  }
+}
+
+// Straight-line move x' = x + (u/gamma) c dt in the local Cartesian frame at
+// azimuth 0; the azimuthal displacement is rotated away (axisymmetry) and u
+// re-expressed in the basis of the new point.  Increments only, no
+// subtraction of absolute radii.
+template <typename R>
+__device__ __forceinline__ void move(R r, R sn, R cs, R th, R dt, const R u[3], R &dr, R &dth, R uo[3]) {
+  const R ig = dt / sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const R d0 = u[0] * ig, d1 = u[1] * ig, d2 = u[2] * ig;
+  const R x = (r + d0) * sn + d1 * cs;
+  const R rc = sqrt(x * x + d2 * d2);
+  const R dR = (x > R(0)) ? d2 * d2 / (rc + x) : rc - x;
+  const R pa = d0 + dR * sn;
+  const R a = r + pa, bb = d1 + dR * cs;
+  const R rnew = sqrt(a * a + bb * bb);
+  dr = (pa * (R(2) * r + pa) + bb * bb) / (rnew + r);
+  const R al = atan2(bb, a);
+  const R ph = atan2(d2, x);
+  dth = al;
+  const R uR = u[0] * sn + u[1] * cs;
+  R sp, cp, sa, ca, s1, c1;
+  sincos(ph, &sp, &cp);
+  sincos(al, &sa, &ca);
+  sincos(th + al, &s1, &c1);
+  const R h = sin(R(0.5) * ph);
+  const R duR = uR * (R(-2) * h * h) + u[2] * sp;
+  uo[0] = u[0] * ca + u[1] * sa + duR * s1;
+  uo[1] = -u[0] * sa + u[1] * ca + duR * c1;
+  uo[2] = -uR * sp + u[2] * cp;
+}
+
+// Charge-conserving deposit for linear shapes (Esirkepov decomposition) in
+// the logical (xi, eta) plane: charge through each dual face over the exact
+// face area and dt gives J_r, J_th; J_ph uses mid-point weights over the
+// node dual volume.  (x0, y0) in [0,1) is the start offset in cell (i0, j0);
+// (X1, Y1) the end point relative to node (i0, j0).
+template <typename R, typename M>
+__device__ __forceinline__ void deposit(const M &m, const Params<R> &p, R qw, int i0, int j0, R x0, R y0,
+                                        R X1, R Y1, R vphi) {
+  const int nr = p.nr, nt = p.nt;
+  R s0x[4] = {R(0), R(1) - x0, x0, R(0)}, s0y[4] = {R(0), R(1) - y0, y0, R(0)};
+  R s1x[4] = {0, 0, 0, 0}, s1y[4] = {0, 0, 0, 0}, dsx[4], dsy[4];
+  const int kx = (int)floor(X1), ky = (int)floor(Y1);
+  {
+    const R fr = X1 - R(kx);
+    s1x[kx + 1] = R(1) - fr; s1x[kx + 2] = fr;
+    if (kx == 0) { const R d = X1 - x0; dsx[0] = R(0); dsx[1] = -d; dsx[2] = d; dsx[3] = R(0); }
+    else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) dsx[a] = s1x[a] - s0x[a];
+    }
+  }
+  {
+    const R fr = Y1 - R(ky);
+    s1y[ky + 1] = R(1) - fr; s1y[ky + 2] = fr;
+    if (ky == 0) { const R d = Y1 - y0; dsy[0] = R(0); dsy[1] = -d; dsy[2] = d; dsy[3] = R(0); }
+    else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) dsy[a] = s1y[a] - s0y[a];
+    }
+  }
+  const Tables<R> &t = p.t;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const R sy = R(0.5) * (s0y[b] + s1y[b]);
+    if (sy == R(0)) continue;
+    const int jj = j0 - 1 + b;
+    R acc = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      acc += dsx[a];
+      if (acc == R(0)) continue;
+      const int ii = i0 - 1 + a;
+      if (ii >= 0 && ii < nr && jj >= 0 && jj <= nt) m.add_jr(ii, jj, -qw * acc * sy * t.dep_r[ii] * t.inv_dch[jj]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const R sx = R(0.5) * (s0x[a] + s1x[a]);
+    if (sx == R(0)) continue;
+    const int ii = i0 - 1 + a;
+    R acc = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      acc += dsy[b];
+      if (acc == R(0)) continue;
+      const int jj = j0 - 1 + b;
+      if (ii >= 0 && ii <= nr && jj >= 0 && jj < nt) m.add_jt(ii, jj, -qw * acc * sx * t.dep_t[ii] * t.inv_sh[jj]);
+    }
+  }
+  if (vphi != R(0)) {
+    const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
+    const int km = (int)floor(xm), lm = (int)floor(ym);
+    const R wx = xm - R(km), wy = ym - R(lm);
+    const R qv = qw * vphi;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const int ii = i0 + km + a, jj = j0 + lm + b;
+        const R wg = (a ? wx : R(1) - wx) * (b ? wy : R(1) - wy);
+        if (wg != R(0) && ii >= 0 && ii <= nr && jj >= 0 && jj <= nt)
+          m.add_jp(ii, jj, qv * wg * t.dep_p[ii] * t.inv_dch[jj]);
+      }
+  }
+}
+
+template <typename R> __device__ __forceinline__ R one_minus_ulp();
+template <> __device__ __forceinline__ float one_minus_ulp<float>() { return 0.99999994f; }
+template <> __device__ __forceinline__ double one_minus_ulp<double>() { return 0.99999999999999989; }
+
+struct Tally {
+  double killed, radiated;
+  unsigned nonfinite;
+};
+
+// One particle: gather, push, move, kill rules, deposit, store.
+template <typename R, typename M>
+__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, int64_t q, Tally &tl) {
+  const Species<R> &S = p.sp[s];
+  const int c = S.cell[q];
+  if (c < 0) return;
+  const int nt = p.nt, nr = p.nr;
+  const int i = c / nt, j = c - (c / nt) * nt;
+  const R xo = S.xo[q], yo = S.yo[q], w = S.w[q];
+  R u[3] = {S.ur[q], S.ut[q], S.up[q]};
+  R e[3], b[3], un[3], dg;
+  gather<R>(m, nr, nt, i, j, xo, yo, e, b);
+  const R krr = p.krr[s] * (R)(*p.rr_scale);
+  boris_rr<R>(p.qm[s], krr, p.dt, u, e, b, un, dg);
+  tl.radiated += (double)(w * p.m[s] * dg);
+  const R r = p.t.rn[i] * exp(xo * p.dlog);
+  const R th = (R(j) + yo) * p.dth;
+  if (r * r < p.shell_r2) {  // Sect. 5.1: no momentum across B near the star
+    const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    if (b2 > R(1e-30)) {
+      const R ub = (un[0] * b[0] + un[1] * b[1] + un[2] * b[2]) / b2;
+      un[0] = ub * b[0]; un[1] = ub * b[1]; un[2] = ub * b[2];
+    }
+  }
+  R sn, cs;
+  sincos(th, &sn, &cs);
+  R dr, dth, uo[3];
+  move<R>(r, sn, cs, th, p.dt, un, dr, dth, uo);
+  const R ginv = R(1) / sqrt(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+  R X1 = xo + log1p(dr / r) / p.dlog;
+  R Y1 = yo + dth / p.dth;
+  if (!isfinite(X1) || !isfinite(Y1) || !isfinite(uo[0] + uo[1] + uo[2])) {
+    S.cell[q] = -1;
+    tl.nonfinite += 1;
+    return;
+  }
+  if (R(j) + Y1 < R(0)) Y1 = R(-2 * j) - Y1;
+  if (R(j) + Y1 > R(nt)) Y1 = R(2 * (nt - j)) - Y1;
+  bool dead = false;
+  if (R(i) + X1 < R(0)) { X1 = -R(i); dead = true; }
+  else if (R(i) + X1 > p.xi_abs) dead = true;
+  int di = (int)floor(X1), dj = (int)floor(Y1);
+  R xn = X1 - R(di), yn = Y1 - R(dj);
+  if (xn >= R(1)) { xn -= R(1); di += 1; }
+  if (yn >= R(1)) { yn -= R(1); dj += 1; }
+  const int i1 = i + di;
+  int j1 = j + dj;
+  if (j1 >= nt) { j1 = nt - 1; yn = one_minus_ulp<R>(); }
+  if (!dead && m.ff(i1, j1)) dead = true;
+  deposit<R>(m, p, p.q[s] * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
+  if (dead) {
+    S.cell[q] = -1;
+    tl.killed += (double)w;
+    return;
+  }
+  S.cell[q] = i1 * nt + j1;
+  S.xo[q] = xn; S.yo[q] = yn;
+  S.ur[q] = uo[0]; S.ut[q] = uo[1]; S.up[q] = uo[2];
+  if (i1 == 0 && p.inject) atomicAdd(&p.surf[j1], 1);
+}
+
+__device__ __forceinline__ void flush_tally(const Tally &tl, double *acc, unsigned *status) {
+  double k = tl.killed, r = tl.radiated;
+  unsigned nf = tl.nonfinite;
+  for (int o = 16; o > 0; o >>= 1) {
+    k += __shfl_down_sync(0xffffffffu, k, o);
+    r += __shfl_down_sync(0xffffffffu, r, o);
+    nf += __shfl_down_sync(0xffffffffu, nf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (k != 0.0) atomicAdd(&acc[1], k);
+    if (r != 0.0) atomicAdd(&acc[2], r);
+    if (nf) { atomicAdd(&acc[3], (double)nf); atomicOr(status, kStNonfinite); }
+  }
+}
+
+// ----------------------------------------------------------- tail kernel
+template <typename R>
+__global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
+  GlobalMesh<R> m(p);
+  Tally tl{0.0, 0.0, 0u};
+  for (int s = 0; s < p.n_species; ++s) {
+    const int64_t n0 = p.count_sorted[s], n1 = p.count[s];
+    for (int64_t q = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1;
+         q += (int64_t)gridDim.x * blockDim.x)
+      push_one<R>(m, p, s, q, tl);
+  }
+  flush_tally(tl, p.acc, p.status);
+}
+
+// ---------------------------------------------------------- tiled kernel
+// Region of a tile: cells [ti*TR - H, (ti+1)*TR + H) (and likewise in theta)
+// widened by the stencil: one node below, two above.
+template <typename R>
+__global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, int halo) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
+  R *base = reinterpret_cast<R *>(smem);
+  SharedMesh<R> m;
+  m.s_er = base; m.s_et = base + area; m.s_ep = base + 2 * area;
+  m.s_br = base + 3 * area; m.s_bt = base + 4 * area; m.s_bp = base + 5 * area;
+  m.s_jr = base + 6 * area; m.s_jt = base + 7 * area; m.s_jp = base + 8 * area;
+  m.s_ff = reinterpret_cast<uint8_t *>(base + 9 * area);
+  m.lt = lt;
+  __shared__ int s_item;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  GlobalMesh<R> g(p);
+  Tally tl{0.0, 0.0, 0u};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(wl.next, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= *wl.n_items) break;
+    const int4 item = wl.items[it];
+    const int s = item.x, tile = item.y;
+    const int ti = tile / p.ntt, tj = tile - ti * p.ntt;
+    m.i0 = ti * p.tile_r - halo - 1;
+    m.j0 = tj * p.tile_t - halo - 1;
+    // stage E, B, flags; clear J
+    for (int k = threadIdx.x; k < area; k += blockDim.x) {
+      const int a = k / lt, c = k - a * lt;
+      const int gi = m.i0 + a, gj = m.j0 + c;
+      const bool okr = gi >= 0, okj = gj >= 0;
+      m.s_er[k] = (okr && okj && gi < nr && gj <= nt) ? p.f.er[ix(gi, gj, n1)] : R(0);
+      m.s_et[k] = (okr && okj && gi <= nr && gj < nt) ? p.f.et[ix(gi, gj, nt)] : R(0);
+      m.s_ep[k] = (okr && okj && gi <= nr && gj <= nt) ? p.f.ep[ix(gi, gj, n1)] : R(0);
+      m.s_br[k] = (okr && okj && gi <= nr && gj < nt) ? p.f.br[ix(gi, gj, nt)] : R(0);
+      m.s_bt[k] = (okr && okj && gi < nr && gj <= nt) ? p.f.bt[ix(gi, gj, n1)] : R(0);
+      m.s_bp[k] = (okr && okj && gi < nr && gj < nt) ? p.f.bp[ix(gi, gj, nt)] : R(0);
+      m.s_ff[k] = (okr && okj && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
+      m.s_jr[k] = R(0); m.s_jt[k] = R(0); m.s_jp[k] = R(0);
+    }
+    __syncthreads();
+    const int64_t q0 = item.z, q1 = (int64_t)item.z + item.w;
+    // a particle is handled in shared memory when its whole stencil (start
+    // cell -1 .. +2 in both directions) lies inside the region
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      const int c = p.sp[s].cell[q];
+      if (c < 0) continue;
+      const int i = c / nt, j = c - (c / nt) * nt;
+      if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
+        push_one<R>(m, p, s, q, tl);
+      else
+        push_one<R>(g, p, s, q, tl);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < area; k += blockDim.x) {
+      const int a = k / lt, c = k - a * lt;
+      const int gi = m.i0 + a, gj = m.j0 + c;
+      if (gi < 0 || gj < 0) continue;
+      if (m.s_jr[k] != R(0) && gi < nr && gj <= nt) atomicAdd(&p.f.jr[ix(gi, gj, n1)], m.s_jr[k]);
+      if (m.s_jt[k] != R(0) && gi <= nr && gj < nt) atomicAdd(&p.f.jt[ix(gi, gj, nt)], m.s_jt[k]);
+      if (m.s_jp[k] != R(0) && gi <= nr && gj <= nt) atomicAdd(&p.f.jp[ix(gi, gj, n1)], m.s_jp[k]);
+    }
+    __syncthreads();
+  }
+  flush_tally(tl, p.acc, p.status);
+}
+
+template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo) {
+  const size_t area = (size_t)(p.tile_r + 2 * halo + 4) * (p.tile_t + 2 * halo + 4);
+  return area * (9 * sizeof(R) + 1);
+}
+
+template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, int grid) {
+  k_push_tail<R><<<grid, 256, 0, s>>>(p);
+}
+template <typename R> void launch_push_tiled(const Params<R> &p, const WorkList &wl, int halo,
+                                             cudaStream_t s, int grid) {
+  k_push_tiled<R><<<grid, 256, push_tiled_smem(p, halo), s>>>(p, wl, halo);
+}
+
+// ------------------------------------------------------------- injection
+// Top-up of each eligible surface cell to its target (fixed at init from
+// kappa n_GJ V / w, Sects. 4 and 5.1): n_new(j) = max(0, target_j - surf_j/2)
+// co-located pairs, offsets from Philox4x32-10 keyed (seed; step, j, k),
+// corotating momentum, appended in (j, k) order.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// one block: exclusive scan of the per-cell counts, reserve slots
+template <typename R>
+__global__ void __launch_bounds__(1024) k_inject_scan(Params<R> p) {
+  __shared__ int s_w[32];
+  __shared__ int s_carry;
+  const int nt = p.nt;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int seg = 0; seg < nt; seg += blockDim.x) {
+    const int j = seg + threadIdx.x;
+    int v = 0;
+    if (j < nt) {
+      const int need = p.target[j] - p.surf[j] / 2;
+      v = need > 0 ? need : 0;
+      p.surf[j] = 0;  // consumed: cleared for the next step
+    }
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    int off = s_carry;
+    for (int w = 0; w < wid; ++w) off += s_w[w];
+    if (j < nt) p.inj_prefix[j] = off + x - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = off + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int total = s_carry;
+    p.inj_prefix[nt] = total;
+    const int npair = p.n_species < 2 ? p.n_species : 2;
+    for (int s = 0; s < npair; ++s) {
+      const long long base = p.count[s];
+      p.inj_base[s] = base;
+      long long end = base + total;
+      if (end > p.cap) { end = p.cap; atomicOr(p.status, kStCapacity); }
+      p.count[s] = end;
+    }
+    atomicAdd(&p.acc[0], (double)total * (double)p.w_inj * npair);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_inject_write(Params<R> p) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nt = p.nt;
+  if (j < nt) {
+    const int k0 = p.inj_prefix[j], n = p.inj_prefix[j + 1] - k0;
+    const long long step = *p.step;
+    const int npair = p.n_species < 2 ? p.n_species : 2;
+    for (int k = 0; k < n; ++k) {
+      uint32_t c[4] = {(uint32_t)step, (uint32_t)((unsigned long long)step >> 32), (uint32_t)j, (uint32_t)k};
+      philox4x32_10(c, p.seed_lo, p.seed_hi);
+      const R ox = (R)(c[0] >> 8) * R(1.0 / 16777216.0);
+      const R oy = (R)(c[1] >> 8) * R(1.0 / 16777216.0);
+      const R r = p.t.rn[0] * exp(ox * p.dlog);
+      const R v = p.omega * r * sin((R(j) + oy) * p.dth);
+      const R uphi = v / sqrt(R(1) - v * v);
+      for (int s = 0; s < npair; ++s) {
+        const long long q = p.inj_base[s] + k0 + k;
+        if (q >= p.count[s]) continue;  // capacity reached (flagged by the scan)
+        Species<R> S = p.sp[s];
+        S.cell[q] = j;
+        S.xo[q] = ox; S.yo[q] = oy;
+        S.ur[q] = R(0); S.ut[q] = R(0); S.up[q] = uphi;
+        S.w[q] = p.w_inj;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_step_done(Params<R> p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p.step += 1;
+}
+
+template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s) {
+  if (p.inject) {
+    k_inject_scan<R><<<1, 1024, 0, s>>>(p);
+    k_inject_write<R><<<(p.nt + 127) / 128, 128, 0, s>>>(p);
+  }
+  k_step_done<R><<<1, 32, 0, s>>>(p);
+}
+template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s) {
+  k_step_done<R><<<1, 32, 0, s>>>(p);
+}
+template <typename R> cudaError_t set_push_smem(size_t bytes) {
+  return cudaFuncSetAttribute(k_push_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define HFF_INST(R)                                                                         \
+  template size_t push_tiled_smem<R>(const Params<R> &, int);                               \
+  template void launch_push_tail<R>(const Params<R> &, cudaStream_t, int);                  \
+  template void launch_push_tiled<R>(const Params<R> &, const WorkList &, int, cudaStream_t, int); \
+  template void launch_inject<R>(const Params<R> &, cudaStream_t);                          \
+  template void launch_step_done<R>(const Params<R> &, cudaStream_t);                       \
+  template cudaError_t set_push_smem<R>(size_t);
+HFF_INST(float)
+HFF_INST(double)
+#undef HFF_INST
+
+}  // namespace hff

@@ -1,0 +1,313 @@
+// sort.cu -- stable sort of one species' particles by tile key with
+// compaction of removed particles, and the (species, tile, chunk) work list
+// of the tiled push.
+//
+// Key = tile index (cells grouped in tile_r x tile_t blocks, row-major over
+// tiles); removed particles get the key ntiles and sort last.  The sort is an
+// LSD radix sort over 8-bit digits of (key, index) pairs.  Each pass: per-block
+// digit histograms (2048 elements per block), one exclusive scan over the
+// digit-major histogram matrix, and a stable scatter in which every element's
+// rank inside its block comes from warp match masks, so equal keys keep their
+// order (the result equals a stable sort by key).  The particle payload moves
+// once, in a final gather.
+#include "hff_common.cuh"
+
+namespace hff {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortBlock = kSortThreads * kSortItems;  // 2048 elements
+constexpr int kScanBlock = 4096;
+
+__device__ __forceinline__ uint32_t tile_key(int cell, int nt, int tile_r, int tile_t, int ntt,
+                                             uint32_t dead) {
+  if (cell < 0) return dead;
+  const int i = cell / nt, j = cell - (cell / nt) * nt;
+  return (uint32_t)((i / tile_r) * ntt + j / tile_t);
+}
+
+struct SortArgs {
+  const int32_t *cell;      // first pass: keys are computed from the cells
+  const uint32_t *keys_in;  // later passes
+  const uint32_t *idx_in;
+  uint32_t *keys_out, *idx_out;
+  uint32_t *hist;
+  int64_t n;
+  int nb, shift, nt, tile_r, tile_t, ntt;
+  uint32_t dead;
+  bool first;
+};
+
+__device__ __forceinline__ uint32_t load_key(const SortArgs &a, int64_t e) {
+  return a.first ? tile_key(a.cell[e], a.nt, a.tile_r, a.tile_t, a.ntt, a.dead) : a.keys_in[e];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t e = base + r * kSortThreads + threadIdx.x;
+    if (e < a.n) atomicAdd(&h[(load_key(a, e) >> a.shift) & 255u], 1u);
+  }
+  __syncthreads();
+  a.hist[(int64_t)threadIdx.x * a.nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of n words in place: block sums, scan of the sums, apply
+__global__ void __launch_bounds__(1024) k_scan_sums(const uint32_t *x, int64_t n, uint32_t *part) {
+  __shared__ uint32_t w[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  uint32_t s = 0;
+  for (int k = threadIdx.x; k < kScanBlock; k += 1024) {
+    const int64_t e = base + k;
+    if (e < n) s += x[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t v = w[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *w, uint32_t &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) w[wid] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = (threadIdx.x < nw) ? w[threadIdx.x] : 0u;
+    uint32_t z = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (threadIdx.x >= o) z += y;
+    }
+    w[threadIdx.x] = z - t;  // exclusive warp offsets
+    if (threadIdx.x == 31) w[32] = z;
+  }
+  __syncthreads();
+  const uint32_t r = w[wid] + x - v;
+  total = w[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_parts(uint32_t *part, int m) {
+  __shared__ uint32_t w[33];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int seg = 0; seg < m; seg += 1024) {
+    const int k = seg + threadIdx.x;
+    const uint32_t v = (k < m) ? part[k] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, w, tot);
+    if (k < m) part[k] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(uint32_t *x, int64_t n, const uint32_t *part) {
+  __shared__ uint32_t w[33];
+  __shared__ uint32_t carry;
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  if (threadIdx.x == 0) carry = part[blockIdx.x];
+  __syncthreads();
+  for (int seg = 0; seg < kScanBlock; seg += 1024) {
+    const int64_t e = base + seg + threadIdx.x;
+    const uint32_t v = (e < n) ? x[e] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, w, tot);
+    if (e < n) x[e] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+// stable scatter: element order inside a block is (round, warp, lane)
+__global__ void __launch_bounds__(kSortThreads) k_scatter(SortArgs a) {
+  constexpr int kW = kSortThreads / 32;
+  __shared__ uint32_t s_base[256];        // global offset of each digit for this block
+  __shared__ uint16_t s_cnt[kW][256];     // per-warp digit counts of the round
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  s_base[threadIdx.x] = a.hist[(int64_t)threadIdx.x * a.nb + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int r = 0; r < kSortItems; ++r) {
+    for (int w = 0; w < kW; ++w) s_cnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t e = base + r * kSortThreads + threadIdx.x;
+    const bool ok = e < a.n;
+    uint32_t key = 0, val = 0, d = 256;
+    if (ok) {
+      key = load_key(a, e);
+      val = a.first ? (uint32_t)e : a.idx_in[e];
+      d = (key >> a.shift) & 255u;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt_mask);
+    if (ok && rank == 0) s_cnt[wid][d] = (uint16_t)__popc(peers);
+    __syncthreads();
+    // thread t owns digit t: exclusive offsets over the warps, then advance
+    {
+      uint32_t acc = 0;
+      for (int w = 0; w < kW; ++w) {
+        const uint32_t c = s_cnt[w][threadIdx.x];
+        s_cnt[w][threadIdx.x] = (uint16_t)acc;
+        acc += c;
+      }
+      __syncthreads();
+      if (ok) {
+        const uint32_t pos = s_base[d] + s_cnt[wid][d] + rank;
+        a.keys_out[pos] = key;
+        a.idx_out[pos] = val;
+      }
+      __syncthreads();
+      s_base[threadIdx.x] += acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_gather(Species<R> src, Species<R> dst, const uint32_t *idx,
+                                                const uint32_t *keys, uint32_t dead, int64_t n,
+                                                long long *count, long long *count_sorted, int species) {
+  // live count = first index whose key is dead (keys are sorted)
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    if (keys[q] == dead) {
+      if (q == 0 || keys[q - 1] != dead) { count[species] = q; count_sorted[species] = q; }
+      dst.cell[q] = -1;  // every slot past the live count holds a removed particle
+      continue;
+    }
+    if (q == n - 1) { count[species] = n; count_sorted[species] = n; }
+    const uint32_t k = idx[q];
+    dst.cell[q] = src.cell[k];
+    dst.xo[q] = src.xo[k]; dst.yo[q] = src.yo[k];
+    dst.ur[q] = src.ur[k]; dst.ut[q] = src.ut[k]; dst.up[q] = src.up[k];
+    dst.w[q] = src.w[k];
+  }
+}
+
+__global__ void k_set_count(long long *count, long long *count_sorted, int species, long long v) {
+  count[species] = v;
+  count_sorted[species] = v;
+}
+
+// tile bounds from the sorted keys: start[k] .. end[k]
+__global__ void k_bounds(const uint32_t *keys, int64_t n, uint32_t dead, int *start, int *end) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[q];
+    if (k == dead) continue;
+    if (q == 0 || keys[q - 1] != k) start[k] = (int)q;
+    if (q == n - 1 || keys[q + 1] != k) end[k] = (int)(q + 1);
+  }
+}
+
+// append ceil(count/chunk) items per non-empty tile of one species
+__global__ void __launch_bounds__(1024) k_worklist(const int *start, const int *end, int ntiles, int species,
+                                                   int chunk, int4 *items, int *n_items, int max_items,
+                                                   bool first, unsigned *status) {
+  __shared__ uint32_t w[33];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = first ? 0u : (uint32_t)*n_items;
+  __syncthreads();
+  for (int seg = 0; seg < ntiles; seg += 1024) {
+    const int k = seg + threadIdx.x;
+    int cnt = 0;
+    if (k < ntiles) cnt = end[k] - start[k];
+    const uint32_t ni = cnt > 0 ? (uint32_t)((cnt + chunk - 1) / chunk) : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(ni, w, tot);
+    for (uint32_t c = 0; c < ni; ++c) {
+      const uint32_t slot = carry + ex + c;
+      if ((int)slot < max_items) {
+        const int s0 = start[k] + (int)c * chunk;
+        const int len = min(chunk, end[k] - s0);
+        items[slot] = make_int4(species, k, s0, len);
+      } else {
+        atomicOr(status, kStWorklist);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_items = (int)min((int)carry, max_items);
+}
+
+static int bits_for(uint32_t v) {
+  int b = 0;
+  while ((1ull << b) <= v) ++b;
+  return b;
+}
+
+template <typename R>
+void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortScratch &ss, cudaStream_t st) {
+  // The slot count lives on the device, so (to stay capturable in a CUDA
+  // graph) the passes run over the whole capacity; every slot at or past the
+  // count holds cell = -1 (kept so by hff_init, this gather and injection),
+  // so those slots sort last as removed particles.
+  const int64_t n = ss.cap;
+  const uint32_t dead = (uint32_t)ss.ntiles;
+  const int nbits = bits_for(dead);
+  const int passes = (nbits + 7) / 8;
+  const int nb = (int)((n + kSortBlock - 1) / kSortBlock);
+  const int64_t hn = (int64_t)nb * 256;
+  const int nparts = (int)((hn + kScanBlock - 1) / kScanBlock);
+  SortArgs a{};
+  a.cell = p.sp[s].cell;
+  a.n = n;
+  a.nb = nb;
+  a.nt = p.nt; a.tile_r = p.tile_r; a.tile_t = p.tile_t; a.ntt = p.ntt;
+  a.dead = dead;
+  a.hist = ss.hist;
+  uint32_t *ko = ss.keys_a, *io = ss.idx_a, *ki = ss.keys_b, *ii = ss.idx_b;
+  for (int pass = 0; pass < passes; ++pass) {
+    a.first = (pass == 0);
+    a.shift = 8 * pass;
+    a.keys_in = ki; a.idx_in = ii;
+    a.keys_out = ko; a.idx_out = io;
+    k_hist<<<nb, kSortThreads, 0, st>>>(a);
+    k_scan_sums<<<nparts, 1024, 0, st>>>(ss.hist, hn, ss.part);
+    k_scan_parts<<<1, 1024, 0, st>>>(ss.part, nparts);
+    k_scan_apply<<<nparts, 1024, 0, st>>>(ss.hist, hn, ss.part);
+    k_scatter<<<nb, kSortThreads, 0, st>>>(a);
+    uint32_t *t = ki; ki = ko; ko = t;
+    t = ii; ii = io; io = t;
+  }
+  // ki / ii now hold the sorted keys and indices
+  k_set_count<<<1, 1, 0, st>>>(p.count, p.count_sorted, s, (long long)n);
+  k_gather<R><<<1216, 256, 0, st>>>(p.sp[s], dst, ii, ki, dead, n, p.count, p.count_sorted, s);
+  cudaMemsetAsync(ss.tile_start, 0, sizeof(int) * (ss.ntiles + 1), st);
+  cudaMemsetAsync(ss.tile_end, 0, sizeof(int) * (ss.ntiles + 1), st);
+  k_bounds<<<1216, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
+}
+
+template <typename R>
+void launch_worklist(const Params<R> &p, const SortScratch *ss, const WorkList &wl, int species, int first,
+                     cudaStream_t st) {
+  k_worklist<<<1, 1024, 0, st>>>(ss->tile_start, ss->tile_end, ss->ntiles, species, wl.chunk, wl.items,
+                                 wl.n_items, wl.max_items, first != 0, p.status);
+}
+
+#define HFF_INST(R)                                                                                   \
+  template void launch_sort_species<R>(const Params<R> &, int, Species<R>, const SortScratch &, cudaStream_t); \
+  template void launch_worklist<R>(const Params<R> &, const SortScratch *, const WorkList &, int, int,   \
+                                   cudaStream_t);
+HFF_INST(float)
+HFF_INST(double)
+#undef HFF_INST
+
+}  // namespace hff

@@ -96,7 +96,9 @@ def config(name: str) -> dict:
             c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
         elif kind == "michel":   # monopole, south hemisphere force-free (Sect. 4)
             c = _base(64, 64, 50.0 / 3.0, 5.0, "michel", seed=14)
-            c.update(psi_break=[1.0, 1.0], f_break=[0.0, 1.0], n_pairs=0, steps=10,
+            # sharp cut at the equator (Psi = Psi*), placed a hair below Psi* so
+            # that the equatorial nodes fall deterministically on the force-free side
+            c.update(psi_break=[1.0 - 1e-4, 1.0 - 1e-4], f_break=[0.0, 1.0], n_pairs=0, steps=10,
                      precision="fp32", place="uniform", momenta="maxwell")
         else:
             raise KeyError(name)

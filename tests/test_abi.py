@@ -1,0 +1,71 @@
+"""CPU-side checks of the C ABI: the library loads without a GPU, exports
+every function declared in include/hff.h, and validates configurations and
+plans memory on the host (no device calls)."""
+import os
+import re
+
+import pytest
+
+from paper_2406_14512_gb300 import build as hff_build
+from paper_2406_14512_gb300 import hff, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hff_build.build()
+    return hff.load()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "hff.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(hff_[a-z_]+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_binding_symbols():
+    assert declared() == sorted(hff.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_plan_sizes_scale_with_grid_and_capacity(lib):
+    c1 = hff.config_struct(dict(workloads.config("c1"), capacity=300_000))
+    b1 = hff.hff_plan(c1)
+    c2 = hff.config_struct(dict(workloads.config("c1"), capacity=600_000))
+    b2 = hff.hff_plan(c2)
+    assert b2 > b1 > 0
+    c3 = workloads.config("c3")
+    c3["capacity"] = int(1.1 * c3["n_pairs"])
+    b3 = hff.hff_plan(hff.config_struct(c3))
+    # 2 species x 1.65e8 slots x 28 B x 2 sort buffers, 16 B of sort keys per
+    # slot, and about 1.5 GB of fields: ~23 GB of the 280 GB of HBM
+    assert 15e9 < b3 < 40e9, b3
+
+
+@pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=9), dict(n_breaks_bad=True),
+                                 dict(r_abs=1e9), dict(precision_bad=True)])
+def test_invalid_configs_are_rejected(lib, bad):
+    cfg = workloads.config("small_pic")
+    cfg.update(capacity=10)
+    c = hff.config_struct(cfg)
+    if "nr" in bad:
+        c.nr = bad["nr"]
+    if "courant" in bad:
+        c.courant = bad["courant"]
+    if "sort_every" in bad:
+        c.sort_every = bad["sort_every"]
+    if "n_breaks_bad" in bad:
+        c.n_breaks = 2
+        c.psi_break[0], c.psi_break[1] = 2.0, 1.0
+    if "r_abs" in bad:
+        c.r_abs = bad["r_abs"]
+    if "precision_bad" in bad:
+        c.precision = 7
+    with pytest.raises(hff.HffError) as e:
+        hff.hff_plan(c)
+    assert e.value.code == hff.HFF_ERR_ARG
+    assert hff.hff_last_error()

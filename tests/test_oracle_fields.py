@@ -237,7 +237,7 @@ def test_blend_table1(oracle_mod):
                    (2.3, 0.0), (2.35, 0.5), (2.4, 1.0), (10.0, 1.0)]:
         assert abs(o.blend(psi * u) - f) < 1e-12, psi
     m = oracle_mod.Oracle(workloads.config("small_michel"))
-    assert m.blend(0.999) == 0.0 and m.blend(1.0) == 1.0 and m.blend(1.5) == 1.0
+    assert m.blend(0.998) == 0.0 and m.blend(1.0) == 1.0 and m.blend(1.5) == 1.0
 
 
 def test_courant_matches_table1_ratio(oracle_mod):
