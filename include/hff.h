@@ -41,7 +41,9 @@
  * bytes one instance needs; the caller allocates them (for instance as a torch
  * uint8 tensor), passes them to hff_init and keeps them alive until
  * hff_destroy returns.  The library allocates no device memory of its own
- * apart from CUDA graphs.  All work is queued on the caller's stream.
+ * apart from CUDA graphs; each handle holds a few KB of pinned host memory
+ * for per-step scalars and counter readback.  All work is queued on the
+ * caller's stream.
  *
  * Errors: every function returns HFF_OK (0) or a negative HFF_ERR_* code;
  * hff_last_error() gives a message for the calling thread.  Faults detected on
@@ -131,6 +133,9 @@ typedef struct hff_info {
   int32_t tile_r, tile_t, sort_every, precision;
   int64_t kernels_per_step; /* kernels one step launches (sort steps: more)      */
   int64_t kernels_launched; /* kernels launched by hff_step since hff_init       */
+  int64_t pushed_tiled;     /* particle pushes by the tile-staged kernel (total) */
+  int64_t pushed_tail;      /* particle pushes by the global-memory kernel       */
+  int64_t readback_bytes;   /* bytes hff_get_info copies device -> host          */
 } hff_info;
 
 typedef struct hff_particle_view {
@@ -186,6 +191,12 @@ int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int 
 /* Advance nsteps whole steps (asynchronous on the stream; one CUDA graph per
  * step, replayed).  Returns the latched device status of earlier steps. */
 int hff_step(hff_handle *h, int32_t nsteps);
+
+/* As hff_step, but for step k records the caller's CUDA events ev_begin[k]
+ * and ev_end[k] (cudaEvent_t) on the stream immediately before and after the
+ * tile-staged push kernel, so that its duration can be timed inside a run of
+ * whole steps.  The step then runs as three graph launches instead of one. */
+int hff_step_timed(hff_handle *h, int32_t nsteps, void *const *ev_begin, void *const *ev_end);
 
 /* Advance nsteps steps running only the stages in the HFF_ST_* mask (eager
  * launches; used to test the parts of a step). */

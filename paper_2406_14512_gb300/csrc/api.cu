@@ -134,7 +134,7 @@ struct Offsets {
   size_t f[19];          // er et ep br bt bp br0 bt0 bp0 jr jt jp psi jpr jpt jpp der det dep
   size_t ffcell;
   size_t tab_r[16];      // rn inv_rn rh inv_rh c_b2 c_bp2 c_e2 c_ep2 rho_a rho_b rh2 dep_r dep_t dep_p sig_n sig_h
-  size_t tab_c[5];       // sn sh inv_sh inv_dcp inv_dch
+  size_t tab_c[6];       // sn sh inv_sh inv_dcp inv_dch cn
   size_t r2n, dcp;       // FP64 prefix factors
   size_t dg[9];          // FP64 diag geometry: rn rh rlo rhi sn sh dch tlo thi
   size_t part[2][kMaxSpecies][7];
@@ -156,6 +156,7 @@ struct Small {  // device counters, one 256-byte block
   double rr;
   double kin[kMaxSpecies];
   double cnt[kMaxSpecies];
+  unsigned long long pushed[2];
   unsigned status;
   int n_items;
   int next;
@@ -175,8 +176,8 @@ void layout(const hff_config &c, Offsets &o) {
   o.ffcell = L.take(nr * nt);
   const size_t rl[16] = {nr + 1, nr + 1, nr, nr, nr, nr, nr + 1, nr + 1, nr + 1, nr + 1, nr, nr, nr + 1, nr + 1, nr + 1, nr};
   for (int k = 0; k < 16; ++k) o.tab_r[k] = L.take(rl[k] * R);
-  const size_t cl[5] = {nt + 1, nt, nt, nt, nt + 1};
-  for (int k = 0; k < 5; ++k) o.tab_c[k] = L.take(cl[k] * R);
+  const size_t cl[6] = {nt + 1, nt, nt, nt, nt + 1, nt + 1};
+  for (int k = 0; k < 6; ++k) o.tab_c[k] = L.take(cl[k] * R);
   o.r2n = L.take((nr + 1) * 8);
   o.dcp = L.take(nt * 8);
   const size_t dl[9] = {nr + 1, nr, nr + 1, nr + 1, nt + 1, nt, nt + 1, nt + 1, nt + 1};
@@ -234,9 +235,17 @@ struct hff_handle {
   int parity = 0;
   int64_t step = 0;
   cudaGraphExec_t g_step[2] = {nullptr, nullptr}, g_sort[2] = {nullptr, nullptr};
-  int64_t k_step[2] = {0, 0}, k_sort[2] = {0, 0};
+  cudaGraphExec_t g_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int64_t k_step[2] = {0, 0}, k_sort[2] = {0, 0}, k_part[2][3] = {{0, 0, 0}, {0, 0, 0}};
   int64_t launched = 0;
+  // pinned host staging: per-step scalars (a ring, so queued copies never
+  // see a later value) and the counter readback
+  double *pin_scalar = nullptr;
+  unsigned pin_next = 0;
+  Small *pin_small = nullptr;
 };
+
+constexpr unsigned kScalarRing = 1024;
 
 namespace {
 
@@ -255,6 +264,8 @@ void fill_params(hff_handle *h) {
     p.nr = c.nr; p.nt = c.nt;
     p.dt = (R)h->dt; p.dlog = (R)h->g.dlog; p.dth = (R)h->g.dth; p.omega = (R)(1.0 / c.r_lc);
     p.r_min = (R)c.r_min; p.xi_abs = (R)h->xi_abs; p.shell_r2 = (R)(c.shell_r * c.shell_r);
+    p.inv_dlog = (R)(1.0 / h->g.dlog); p.inv_dth = (R)(1.0 / h->g.dth);
+    p.small_grid = (h->g.dlog < 0.03 && h->g.dth < 0.03) ? 1 : 0;
     p.n_breaks = c.n_breaks;
     for (int k = 0; k < kMaxBreaks; ++k) {
       p.psi_break[k] = (R)(c.psi_break[k] * h->psi_unit);
@@ -278,8 +289,8 @@ void fill_params(hff_handle *h) {
     const R **tr[16] = {&t.rn, &t.inv_rn, &t.rh, &t.inv_rh, &t.c_b2, &t.c_bp2, &t.c_e2, &t.c_ep2,
                         &t.rho_a, &t.rho_b, &t.rh2, &t.dep_r, &t.dep_t, &t.dep_p, &t.sig_n, &t.sig_h};
     for (int k = 0; k < 16; ++k) *tr[k] = reinterpret_cast<const R *>(b + o.tab_r[k]);
-    const R **tc[5] = {&t.sn, &t.sh, &t.inv_sh, &t.inv_dcp, &t.inv_dch};
-    for (int k = 0; k < 5; ++k) *tc[k] = reinterpret_cast<const R *>(b + o.tab_c[k]);
+    const R **tc[6] = {&t.sn, &t.sh, &t.inv_sh, &t.inv_dcp, &t.inv_dch, &t.cn};
+    for (int k = 0; k < 6; ++k) *tc[k] = reinterpret_cast<const R *>(b + o.tab_c[k]);
     t.r2n = reinterpret_cast<const double *>(b + o.r2n);
     t.dcp = reinterpret_cast<const double *>(b + o.dcp);
     Fields<R> &f = p.f;
@@ -307,6 +318,7 @@ void fill_params(hff_handle *h) {
     p.inject = c.inject;
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
+    p.pushed = h->small->pushed;
     p.status = &h->small->status;
     p.tile_r = tile_r_of(c); p.tile_t = tile_t_of(c); p.ntt = o.ntt;
   }
@@ -365,17 +377,18 @@ int init_state(hff_handle *h) {
   }
   for (int k = 0; k < 16; ++k)
     if ((rc = upload<R>(h, h->o.tab_r[k], T[k])) != HFF_OK) return rc;
-  std::vector<double> C[5];
+  std::vector<double> C[6];
   for (int j = 0; j <= nt; ++j) {
     C[0].push_back(std::sin(g.tn(j)));
     C[4].push_back(1.0 / g.dch(j));
+    C[5].push_back(std::cos(g.tn(j)));
   }
   for (int j = 0; j < nt; ++j) {
     C[1].push_back(std::sin(g.th(j)));
     C[2].push_back(1.0 / std::sin(g.th(j)));
     C[3].push_back(1.0 / g.dcp(j));
   }
-  for (int k = 0; k < 5; ++k)
+  for (int k = 0; k < 6; ++k)
     if ((rc = upload<R>(h, h->o.tab_c[k], C[k])) != HFF_OK) return rc;
   std::vector<double> r2n, dcp;
   for (int i = 0; i <= nr; ++i) r2n.push_back(g.rn(i) * g.rn(i));
@@ -457,20 +470,23 @@ int init_state(hff_handle *h) {
 }
 
 // --------------------------------------------------------- step enqueueing
+// parts: 1 = up to the tiled push, 2 = the tiled push, 4 = the rest
 template <typename R>
-int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s) {
+int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts = 7) {
   Params<R> &p = params<R>(h)[par];
-  if (stages & HFF_ST_NODE) {
+  if ((parts & 1) && (stages & HFF_ST_NODE)) {
     launch_psi<R>(p, s);
     launch_node_a<R>(p, s);
   }
-  if (stages & HFF_ST_PUSH) {
-    if (h->c.sort_every > 0) {
-      CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
-      launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid);
-    }
-    launch_push_tail<R>(p, s, h->tail_grid);
+  if ((parts & 1) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
+    CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
+  if ((parts & 2) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
+    launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid);
+  if (!(parts & 4)) {
+    CK(cudaGetLastError());
+    return HFF_OK;
   }
+  if (stages & HFF_ST_PUSH) launch_push_tail<R>(p, s, h->tail_grid);
   if (stages & HFF_ST_FARADAY1) launch_faraday<R>(p, R(0.5), false, s);
   if (stages & HFF_ST_AMPERE) launch_ampere<R>(p, s);
   if (stages & HFF_ST_CORRECT) launch_correct<R>(p, s);
@@ -559,6 +575,39 @@ int do_step(hff_handle *h, int32_t n) {
 }
 
 template <typename R>
+int do_step_timed(hff_handle *h, int32_t n, void *const *evb, void *const *eve) {
+  for (int32_t k = 0; k < n; ++k) {
+    const int par = h->parity;
+    for (int part = 0; part < 3; ++part) {
+      if (!h->g_part[par][part]) {
+        const int mask = 1 << part;
+        int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s, mask); },
+                         &h->g_part[par][part], &h->k_part[par][part]);
+        if (rc != HFF_OK) return rc;
+      }
+    }
+    CK(cudaGraphLaunch(h->g_part[par][0], h->st));
+    if (evb && evb[k]) CK(cudaEventRecord((cudaEvent_t)evb[k], h->st));
+    CK(cudaGraphLaunch(h->g_part[par][1], h->st));
+    if (eve && eve[k]) CK(cudaEventRecord((cudaEvent_t)eve[k], h->st));
+    CK(cudaGraphLaunch(h->g_part[par][2], h->st));
+    h->launched += h->k_part[par][0] + h->k_part[par][1] + h->k_part[par][2];
+    h->step++;
+    if (h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
+      if (!h->g_sort[par]) {
+        int rc = capture(h, [&](cudaStream_t s) { return enqueue_sort<R>(h, par, s); }, &h->g_sort[par],
+                         &h->k_sort[par]);
+        if (rc != HFF_OK) return rc;
+      }
+      CK(cudaGraphLaunch(h->g_sort[par], h->st));
+      h->launched += h->k_sort[par];
+      h->parity ^= 1;
+    }
+  }
+  return HFF_OK;
+}
+
+template <typename R>
 int do_stages(hff_handle *h, int32_t n, int32_t stages) {
   for (int32_t k = 0; k < n; ++k) {
     int rc = enqueue_step<R>(h, h->parity, stages, h->st);
@@ -611,9 +660,18 @@ int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, voi
   h->psi_unit = psi_unit_of(*cfg);
   h->xi_abs = std::log(cfg->r_abs / cfg->r_min) / h->g.dlog;
   h->small = reinterpret_cast<Small *>(h->base + h->o.small);
-  auto bail = [&](int code) { if (h->cap_st) cudaStreamDestroy(h->cap_st); delete h; return code; };
+  auto bail = [&](int code) {
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
+    if (h->pin_scalar) cudaFreeHost(h->pin_scalar);
+    if (h->pin_small) cudaFreeHost(h->pin_small);
+    delete h;
+    return code;
+  };
   if (cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(HFF_ERR_CUDA, "stream create failed"));
+  if (cudaMallocHost(&h->pin_scalar, sizeof(double) * kScalarRing) != cudaSuccess ||
+      cudaMallocHost(&h->pin_small, sizeof(Small)) != cudaSuccess)
+    return bail(fail(HFF_ERR_CUDA, "pinned host staging failed"));
   if (cudaMemsetAsync(h->base, 0, h->o.total, h->st) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "memset failed"));
   const int parities = cfg->sort_every > 0 ? 2 : 1;
   for (int p = 0; p < parities; ++p)
@@ -760,6 +818,12 @@ int hff_step(hff_handle *h, int32_t nsteps) {
   return h->c.precision == HFF_FP64 ? do_step<double>(h, nsteps) : do_step<float>(h, nsteps);
 }
 
+int hff_step_timed(hff_handle *h, int32_t nsteps, void *const *ev_begin, void *const *ev_end) {
+  if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  return h->c.precision == HFF_FP64 ? do_step_timed<double>(h, nsteps, ev_begin, ev_end)
+                                    : do_step_timed<float>(h, nsteps, ev_begin, ev_end);
+}
+
 int hff_step_stages(hff_handle *h, int32_t nsteps, int32_t stages) {
   if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
   return h->c.precision == HFF_FP64 ? do_stages<double>(h, nsteps, stages) : do_stages<float>(h, nsteps, stages);
@@ -768,7 +832,9 @@ int hff_step_stages(hff_handle *h, int32_t nsteps, int32_t stages) {
 int hff_set_scalar(hff_handle *h, int which, double value) {
   if (!h || which != HFF_SCALAR_RR_SCALE) return fail(HFF_ERR_ARG, "bad scalar");
   h->c.rr_scale = value;
-  CK(cudaMemcpyAsync(&h->small->rr, &h->c.rr_scale, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  double *slot = h->pin_scalar + (h->pin_next++ % kScalarRing);
+  *slot = value;
+  CK(cudaMemcpyAsync(&h->small->rr, slot, sizeof(double), cudaMemcpyHostToDevice, h->st));
   return HFF_OK;
 }
 
@@ -840,9 +906,9 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
 
 int hff_get_info(hff_handle *h, hff_info *out) {
   if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
-  Small sm;
-  CK(cudaMemcpyAsync(&sm, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(h->pin_small, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  const Small &sm = *h->pin_small;
   std::memset(out, 0, sizeof(*out));
   out->dt = h->dt;
   out->psi_unit = h->psi_unit;
@@ -854,6 +920,9 @@ int hff_get_info(hff_handle *h, hff_info *out) {
   out->precision = h->c.precision;
   out->kernels_per_step = h->k_step[0] ? h->k_step[0] : h->k_step[1];
   out->kernels_launched = h->launched;
+  out->pushed_tiled = (int64_t)sm.pushed[0];
+  out->pushed_tail = (int64_t)sm.pushed[1];
+  out->readback_bytes = (int64_t)sizeof(Small);
   return HFF_OK;
 }
 
@@ -875,8 +944,12 @@ int hff_destroy(hff_handle *h) {
   for (int p = 0; p < 2; ++p) {
     if (h->g_step[p]) cudaGraphExecDestroy(h->g_step[p]);
     if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
+    for (int k = 0; k < 3; ++k)
+      if (h->g_part[p][k]) cudaGraphExecDestroy(h->g_part[p][k]);
   }
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->pin_scalar) cudaFreeHost(h->pin_scalar);
+  if (h->pin_small) cudaFreeHost(h->pin_small);
   delete h;
   return HFF_OK;
 }

@@ -40,6 +40,7 @@ struct Tables {
   const double *r2n;  // nr+1  r_i^2 (Psi prefix, FP64)
   // columns
   const R *sn;      // nt+1  sin theta_j
+  const R *cn;      // nt+1  cos theta_j
   const R *sh;      // nt    sin theta_{j+1/2}
   const R *inv_sh;  // nt    1/sin theta_{j+1/2}
   const R *inv_dcp; // nt    1/(cos theta_j - cos theta_{j+1})
@@ -68,6 +69,8 @@ template <typename R>
 struct Params {
   int nr, nt;
   R dt, dlog, dth, omega, r_min, xi_abs, shell_r2;
+  R inv_dlog, inv_dth;
+  int small_grid;           // dlog and dtheta both below the series threshold
   int n_breaks;
   R psi_break[kMaxBreaks];  // absolute units
   R f_break[kMaxBreaks];
@@ -89,6 +92,7 @@ struct Params {
   int inject;
   R w_inj;
   double *acc;              // [4] injected, killed, radiated, nonfinite
+  unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel
   unsigned *status;
   int tile_r, tile_t, ntt;  // sort tiles
 };

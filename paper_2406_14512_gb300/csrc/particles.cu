@@ -67,6 +67,33 @@ __device__ __forceinline__ void stag(int c, R o, bool half, int n, int &k0, R &w
   if (k0 > n - 2) { k0 = n - 2; w = R(1); }
 }
 
+// Small-argument Taylor expansions about 0, for the per-step increments that
+// the Courant condition keeps small; callers switch to the library functions
+// outside |x| < kSmall, where every truncation error is below 1e-12.
+constexpr double kSmall = 0.03;
+template <typename R> __device__ __forceinline__ R sin_small(R x) {
+  const R x2 = x * x;
+  return x * (R(1) - x2 * R(1.0 / 6.0) * (R(1) - x2 * R(1.0 / 20.0) * (R(1) - x2 * R(1.0 / 42.0))));
+}
+template <typename R> __device__ __forceinline__ R cos_small(R x) {
+  const R x2 = x * x;
+  return R(1) - R(0.5) * x2 * (R(1) - x2 * R(1.0 / 12.0) * (R(1) - x2 * R(1.0 / 30.0)));
+}
+template <typename R> __device__ __forceinline__ R atan_small(R t) {
+  const R t2 = t * t;
+  return t * (R(1) - t2 * (R(1.0 / 3.0) - t2 * (R(0.2) - t2 * (R(1.0 / 7.0) - t2 * R(1.0 / 9.0)))));
+}
+template <typename R> __device__ __forceinline__ R log1p_small(R x) {
+  return x * (R(1) - x * (R(0.5) - x * (R(1.0 / 3.0) - x * (R(0.25) - x * (R(0.2) - x * (R(1.0 / 6.0) - x * R(1.0 / 7.0)))))));
+}
+template <typename R> __device__ __forceinline__ R exp_small(R x) {
+  return R(1) + x * (R(1) + x * R(0.5) * (R(1) + x * R(1.0 / 3.0) * (R(1) + x * R(0.25) * (R(1) + x * R(0.2) * (R(1) + x * R(1.0 / 6.0))))));
+}
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 template <typename R, typename M, typename Get>
 __device__ __forceinline__ R interp(const M &m, Get g, int i, R wi, int j, R wj) {
   return (R(1) - wi) * ((R(1) - wj) * g(m, i, j) + wj * g(m, i, j + 1)) +
@@ -99,7 +126,7 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
                                          R out[3], R &dgam) {
   const R a = R(0.5) * qm * dt;
   const R um0 = u[0] + a * e[0], um1 = u[1] + a * e[1], um2 = u[2] + a * e[2];
-  const R ig = R(1) / sqrt(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
+  const R ig = rsq(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
   const R t0 = a * b[0] * ig, t1 = a * b[1] * ig, t2 = a * b[2] * ig;
   const R sc = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
   const R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;
@@ -112,14 +139,14 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
   if (krr != R(0)) {
     const R ub0 = R(0.5) * (u[0] + ul0), ub1 = R(0.5) * (u[1] + ul1), ub2 = R(0.5) * (u[2] + ul2);
     const R g2 = R(1) + ub0 * ub0 + ub1 * ub1 + ub2 * ub2;
-    const R ig2 = R(1) / sqrt(g2);
+    const R ig2 = rsq(g2);
     const R be0 = ub0 * ig2, be1 = ub1 * ig2, be2 = ub2 * ig2;
     const R f0 = e[0] + (be1 * b[2] - be2 * b[1]);
     const R f1 = e[1] + (be2 * b[0] - be0 * b[2]);
     const R f2 = e[2] + (be0 * b[1] - be1 * b[0]);
     const R c0 = f1 * be2 - f2 * be1, c1 = f2 * be0 - f0 * be2, c2 = f0 * be1 - f1 * be0;
     const R ff = f0 * f0 + f1 * f1 + f2 * f2;
-    const R bp2 = c0 * c0 + c1 * c1 + c2 * c2 + ff / g2;
+    const R bp2 = c0 * c0 + c1 * c1 + c2 * c2 + ff * ig2 * ig2;
     const R bdot = be0 * e[0] + be1 * e[1] + be2 * e[2];
     const R k = dt * krr;
     const R du0 = k * ((f1 * b[2] - f2 * b[1]) + bdot * e[0] - g2 * bp2 * be0);
@@ -137,9 +164,9 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
 // Straight-line move x' = x + (u/gamma) c dt in the local Cartesian frame at
 // azimuth 0; the azimuthal displacement is rotated away (axisymmetry) and u
 // re-expressed in the basis of the new point.  Increments only, no
-// subtraction of absolute radii.
+// subtraction of absolute radii.  General form (any displacement).
 template <typename R>
-__device__ __forceinline__ void move(R r, R sn, R cs, R th, R dt, const R u[3], R &dr, R &dth, R uo[3]) {
+__device__ __forceinline__ void move_general(R r, R sn, R cs, R dt, const R u[3], R &dr, R &dth, R uo[3]) {
   const R ig = dt / sqrt(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const R d0 = u[0] * ig, d1 = u[1] * ig, d2 = u[2] * ig;
   const R x = (r + d0) * sn + d1 * cs;
@@ -153,10 +180,10 @@ __device__ __forceinline__ void move(R r, R sn, R cs, R th, R dt, const R u[3], 
   const R ph = atan2(d2, x);
   dth = al;
   const R uR = u[0] * sn + u[1] * cs;
-  R sp, cp, sa, ca, s1, c1;
+  R sp, cp, sa, ca;
   sincos(ph, &sp, &cp);
   sincos(al, &sa, &ca);
-  sincos(th + al, &s1, &c1);
+  const R s1 = sn * ca + cs * sa, c1 = cs * ca - sn * sa;  // angle of the new point
   const R h = sin(R(0.5) * ph);
   const R duR = uR * (R(-2) * h * h) + u[2] * sp;
   uo[0] = u[0] * ca + u[1] * sa + duR * s1;
@@ -164,79 +191,120 @@ __device__ __forceinline__ void move(R r, R sn, R cs, R th, R dt, const R u[3], 
   uo[2] = -uR * sp + u[2] * cp;
 }
 
+// The same move for the usual case of a displacement much smaller than the
+// distance to the axis (|d_phi| < 0.03 X and |b| < 0.03 a), where both
+// rotation angles are small: with t = tan(angle), cos = 1/sqrt(1+t^2),
+// sin = t cos and 1 - cos = t^2 / (sqrt(1+t^2)(sqrt(1+t^2)+1)) exactly, and
+// the angle itself from the Taylor series of atan.  Returns false (nothing
+// written) when the displacement is not small.
+template <typename R>
+__device__ __forceinline__ bool move_small(R r, R sn, R cs, R dt, const R u[3], R &dr, R &dth, R uo[3]) {
+  const R ig = dt * rsq(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const R d0 = u[0] * ig, d1 = u[1] * ig, d2 = u[2] * ig;
+  const R x = (r + d0) * sn + d1 * cs;
+  if (!(x > R(0)) || fabs(d2) >= R(kSmall) * x) return false;
+  const R tp = fdiv(d2, x), qp = tp * tp;
+  const R sqp = sqrt(R(1) + qp), cp = R(1) / sqp;
+  const R sp = tp * cp, omc = qp / (sqp * (sqp + R(1)));  // 1 - cos(phi)
+  const R dR = x * omc * sqp;                                // sqrt(x^2+d2^2) - x
+  const R pa = d0 + dR * sn;
+  const R a = r + pa, bb = d1 + dR * cs;
+  if (fabs(bb) >= R(kSmall) * a) return false;
+  const R ta = fdiv(bb, a), qa = ta * ta;
+  const R sqa = sqrt(R(1) + qa), ca = R(1) / sqa, sa = ta * ca;
+  const R rnew = a * sqa;
+  dr = fdiv(pa * (R(2) * r + pa) + bb * bb, rnew + r);
+  dth = atan_small(ta);
+  const R uR = u[0] * sn + u[1] * cs;
+  const R s1 = sn * ca + cs * sa, c1 = cs * ca - sn * sa;
+  const R duR = -uR * omc + u[2] * sp;
+  uo[0] = u[0] * ca + u[1] * sa + duR * s1;
+  uo[1] = -u[0] * sa + u[1] * ca + duR * c1;
+  uo[2] = -uR * sp + u[2] * cp;
+  return true;
+}
+
 // Charge-conserving deposit for linear shapes (Esirkepov decomposition) in
 // the logical (xi, eta) plane: charge through each dual face over the exact
 // face area and dt gives J_r, J_th; J_ph uses mid-point weights over the
 // node dual volume.  (x0, y0) in [0,1) is the start offset in cell (i0, j0);
-// (X1, Y1) the end point relative to node (i0, j0).
+// (X1, Y1) the end point relative to node (i0, j0), in (-1, 2).  The four
+// stencil weights per direction are formed with selects (no indexed arrays),
+// and for a move inside one cell the weight change is +-(X1 - x0) exactly.
+template <typename R>
+__device__ __forceinline__ void shape_delta(R x0, R X1, R s1[4], R ds[4], R sum[4]) {
+  const int k = (X1 < R(0)) ? -1 : (X1 < R(1) ? 0 : 1);
+  s1[0] = (k < 0) ? -X1 : R(0);
+  s1[1] = (k < 0) ? R(1) + X1 : (k == 0 ? R(1) - X1 : R(0));
+  s1[2] = (k == 0) ? X1 : (k > 0 ? R(2) - X1 : R(0));
+  s1[3] = (k > 0) ? X1 - R(1) : R(0);
+  if (k == 0) {
+    const R d = X1 - x0;
+    ds[0] = R(0); ds[1] = -d; ds[2] = d; ds[3] = R(0);
+  } else {
+    ds[0] = s1[0]; ds[1] = s1[1] - (R(1) - x0); ds[2] = s1[2] - x0; ds[3] = s1[3];
+  }
+  sum[0] = R(0.5) * s1[0];
+  sum[1] = R(0.5) * (s1[1] + (R(1) - x0));
+  sum[2] = R(0.5) * (s1[2] + x0);
+  sum[3] = R(0.5) * s1[3];
+}
+
 template <typename R, typename M>
 __device__ __forceinline__ void deposit(const M &m, const Params<R> &p, R qw, int i0, int j0, R x0, R y0,
                                         R X1, R Y1, R vphi) {
   const int nr = p.nr, nt = p.nt;
-  R s0x[4] = {R(0), R(1) - x0, x0, R(0)}, s0y[4] = {R(0), R(1) - y0, y0, R(0)};
-  R s1x[4] = {0, 0, 0, 0}, s1y[4] = {0, 0, 0, 0}, dsx[4], dsy[4];
-  const int kx = (int)floor(X1), ky = (int)floor(Y1);
-  {
-    const R fr = X1 - R(kx);
-    s1x[kx + 1] = R(1) - fr; s1x[kx + 2] = fr;
-    if (kx == 0) { const R d = X1 - x0; dsx[0] = R(0); dsx[1] = -d; dsx[2] = d; dsx[3] = R(0); }
-    else {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) dsx[a] = s1x[a] - s0x[a];
-    }
-  }
-  {
-    const R fr = Y1 - R(ky);
-    s1y[ky + 1] = R(1) - fr; s1y[ky + 2] = fr;
-    if (ky == 0) { const R d = Y1 - y0; dsy[0] = R(0); dsy[1] = -d; dsy[2] = d; dsy[3] = R(0); }
-    else {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) dsy[a] = s1y[a] - s0y[a];
-    }
-  }
+  R s1x[4], dsx[4], mx[4], s1y[4], dsy[4], my[4];
+  shape_delta(x0, X1, s1x, dsx, mx);
+  shape_delta(y0, Y1, s1y, dsy, my);
   const Tables<R> &t = p.t;
+  const R nq = -qw;
+  R ax[3];
+  ax[0] = dsx[0]; ax[1] = ax[0] + dsx[1]; ax[2] = ax[1] + dsx[2];
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const R sy = R(0.5) * (s0y[b] + s1y[b]);
-    if (sy == R(0)) continue;
-    const int jj = j0 - 1 + b;
-    R acc = R(0);
+  for (int a = 0; a < 3; ++a) {
+    if (ax[a] == R(0)) continue;
+    const int ii = i0 - 1 + a;
+    if (ii < 0 || ii >= nr) continue;
+    const R f = nq * ax[a] * t.dep_r[ii];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc += dsx[a];
-      if (acc == R(0)) continue;
-      const int ii = i0 - 1 + a;
-      if (ii >= 0 && ii < nr && jj >= 0 && jj <= nt) m.add_jr(ii, jj, -qw * acc * sy * t.dep_r[ii] * t.inv_dch[jj]);
+    for (int b = 0; b < 4; ++b) {
+      const int jj = j0 - 1 + b;
+      if (my[b] != R(0) && jj >= 0 && jj <= nt) m.add_jr(ii, jj, f * my[b] * t.inv_dch[jj]);
     }
   }
+  R ay[3];
+  ay[0] = dsy[0]; ay[1] = ay[0] + dsy[1]; ay[2] = ay[1] + dsy[2];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const R sx = R(0.5) * (s0x[a] + s1x[a]);
-    if (sx == R(0)) continue;
-    const int ii = i0 - 1 + a;
-    R acc = R(0);
+  for (int b = 0; b < 3; ++b) {
+    if (ay[b] == R(0)) continue;
+    const int jj = j0 - 1 + b;
+    if (jj < 0 || jj >= nt) continue;
+    const R f = nq * ay[b] * t.inv_sh[jj];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      acc += dsy[b];
-      if (acc == R(0)) continue;
-      const int jj = j0 - 1 + b;
-      if (ii >= 0 && ii <= nr && jj >= 0 && jj < nt) m.add_jt(ii, jj, -qw * acc * sx * t.dep_t[ii] * t.inv_sh[jj]);
+    for (int a = 0; a < 4; ++a) {
+      const int ii = i0 - 1 + a;
+      if (mx[a] != R(0) && ii >= 0 && ii <= nr) m.add_jt(ii, jj, f * mx[a] * t.dep_t[ii]);
     }
   }
   if (vphi != R(0)) {
     const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
-    const int km = (int)floor(xm), lm = (int)floor(ym);
+    const int km = (xm < R(0)) ? -1 : (xm < R(1) ? 0 : 1);
+    const int lm = (ym < R(0)) ? -1 : (ym < R(1) ? 0 : 1);
     const R wx = xm - R(km), wy = ym - R(lm);
     const R qv = qw * vphi;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
+      const int ii = i0 + km + a;
+      if (ii < 0 || ii > nr) continue;
+      const R fa = qv * (a ? wx : R(1) - wx) * t.dep_p[ii];
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
-        const int ii = i0 + km + a, jj = j0 + lm + b;
-        const R wg = (a ? wx : R(1) - wx) * (b ? wy : R(1) - wy);
-        if (wg != R(0) && ii >= 0 && ii <= nr && jj >= 0 && jj <= nt)
-          m.add_jp(ii, jj, qv * wg * t.dep_p[ii] * t.inv_dch[jj]);
+        const int jj = j0 + lm + b;
+        const R wg = (b ? wy : R(1) - wy);
+        if (wg != R(0) && fa != R(0) && jj >= 0 && jj <= nt) m.add_jp(ii, jj, fa * wg * t.inv_dch[jj]);
       }
+    }
   }
 }
 
@@ -244,28 +312,42 @@ template <typename R> __device__ __forceinline__ R one_minus_ulp();
 template <> __device__ __forceinline__ float one_minus_ulp<float>() { return 0.99999994f; }
 template <> __device__ __forceinline__ double one_minus_ulp<double>() { return 0.99999999999999989; }
 
+// per-thread counters in the working precision (FP64 only in the warp and
+// global sums)
+template <typename R>
 struct Tally {
-  double killed, radiated;
+  R killed, radiated;
   unsigned nonfinite;
+  unsigned pushed;
 };
 
 // One particle: gather, push, move, kill rules, deposit, store.
 template <typename R, typename M>
-__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, int64_t q, Tally &tl) {
+__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, int64_t q, int c, Tally<R> &tl) {
   const Species<R> &S = p.sp[s];
-  const int c = S.cell[q];
-  if (c < 0) return;
   const int nt = p.nt, nr = p.nr;
-  const int i = c / nt, j = c - (c / nt) * nt;
+  const int i = c / nt, j = c - i * nt;
   const R xo = S.xo[q], yo = S.yo[q], w = S.w[q];
   R u[3] = {S.ur[q], S.ut[q], S.up[q]};
   R e[3], b[3], un[3], dg;
+  tl.pushed += 1;
   gather<R>(m, nr, nt, i, j, xo, yo, e, b);
   const R krr = p.krr[s] * (R)(*p.rr_scale);
   boris_rr<R>(p.qm[s], krr, p.dt, u, e, b, un, dg);
-  tl.radiated += (double)(w * p.m[s] * dg);
-  const R r = p.t.rn[i] * exp(xo * p.dlog);
-  const R th = (R(j) + yo) * p.dth;
+  tl.radiated += w * p.m[s] * dg;
+  // position of the particle: r = r_i exp(xo D), theta = theta_j + yo dtheta
+  const R xl = xo * p.dlog, ya = yo * p.dth;
+  R ex, sa0, ca0;
+  if (p.small_grid) {
+    ex = exp_small(xl);
+    sa0 = sin_small(ya);
+    ca0 = cos_small(ya);
+  } else {
+    ex = exp(xl);
+    sincos(ya, &sa0, &ca0);
+  }
+  const R r = p.t.rn[i] * ex;
+  const R sn = p.t.sn[j] * ca0 + p.t.cn[j] * sa0, cs = p.t.cn[j] * ca0 - p.t.sn[j] * sa0;
   if (r * r < p.shell_r2) {  // Sect. 5.1: no momentum across B near the star
     const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
     if (b2 > R(1e-30)) {
@@ -273,13 +355,12 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
       un[0] = ub * b[0]; un[1] = ub * b[1]; un[2] = ub * b[2];
     }
   }
-  R sn, cs;
-  sincos(th, &sn, &cs);
   R dr, dth, uo[3];
-  move<R>(r, sn, cs, th, p.dt, un, dr, dth, uo);
-  const R ginv = R(1) / sqrt(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
-  R X1 = xo + log1p(dr / r) / p.dlog;
-  R Y1 = yo + dth / p.dth;
+  if (!move_small<R>(r, sn, cs, p.dt, un, dr, dth, uo)) move_general<R>(r, sn, cs, p.dt, un, dr, dth, uo);
+  const R ginv = rsq(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+  const R xr = dr / r;
+  R X1 = xo + ((fabs(xr) < R(kSmall)) ? log1p_small(xr) : log1p(xr)) * p.inv_dlog;
+  R Y1 = yo + dth * p.inv_dth;
   if (!isfinite(X1) || !isfinite(Y1) || !isfinite(uo[0] + uo[1] + uo[2])) {
     S.cell[q] = -1;
     tl.nonfinite += 1;
@@ -301,7 +382,7 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
   deposit<R>(m, p, p.q[s] * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
   if (dead) {
     S.cell[q] = -1;
-    tl.killed += (double)w;
+    tl.killed += w;
     return;
   }
   S.cell[q] = i1 * nt + j1;
@@ -310,18 +391,30 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
   if (i1 == 0 && p.inject) atomicAdd(&p.surf[j1], 1);
 }
 
-__device__ __forceinline__ void flush_tally(const Tally &tl, double *acc, unsigned *status) {
-  double k = tl.killed, r = tl.radiated;
-  unsigned nf = tl.nonfinite;
+// out-of-region fallback of the tiled kernel (kept out of line so that the
+// hot loop stays small)
+template <typename R>
+__device__ __noinline__ void push_one_global(const Params<R> &p, int s, int64_t q, int c, Tally<R> &tl) {
+  GlobalMesh<R> g(p);
+  push_one<R>(g, p, s, q, c, tl);
+}
+
+template <typename R>
+__device__ __forceinline__ void flush_tally(const Tally<R> &tl, double *acc, unsigned *status,
+                                            unsigned long long *pushed) {
+  double k = tl.killed, r = tl.radiated;  // FP64 only for the warp and global sums
+  unsigned nf = tl.nonfinite, np = tl.pushed;
   for (int o = 16; o > 0; o >>= 1) {
     k += __shfl_down_sync(0xffffffffu, k, o);
     r += __shfl_down_sync(0xffffffffu, r, o);
     nf += __shfl_down_sync(0xffffffffu, nf, o);
+    np += __shfl_down_sync(0xffffffffu, np, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (k != 0.0) atomicAdd(&acc[1], k);
     if (r != 0.0) atomicAdd(&acc[2], r);
     if (nf) { atomicAdd(&acc[3], (double)nf); atomicOr(status, kStNonfinite); }
+    if (np) atomicAdd(pushed, (unsigned long long)np);
   }
 }
 
@@ -329,14 +422,16 @@ __device__ __forceinline__ void flush_tally(const Tally &tl, double *acc, unsign
 template <typename R>
 __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
   GlobalMesh<R> m(p);
-  Tally tl{0.0, 0.0, 0u};
+  Tally<R> tl{R(0), R(0), 0u, 0u};
   for (int s = 0; s < p.n_species; ++s) {
     const int64_t n0 = p.count_sorted[s], n1 = p.count[s];
     for (int64_t q = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1;
-         q += (int64_t)gridDim.x * blockDim.x)
-      push_one<R>(m, p, s, q, tl);
+         q += (int64_t)gridDim.x * blockDim.x) {
+      const int c = p.sp[s].cell[q];
+      if (c >= 0) push_one<R>(m, p, s, q, c, tl);
+    }
   }
-  flush_tally(tl, p.acc, p.status);
+  flush_tally(tl, p.acc, p.status, &p.pushed[1]);
 }
 
 // ---------------------------------------------------------- tiled kernel
@@ -355,8 +450,7 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
   m.lt = lt;
   __shared__ int s_item;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
-  GlobalMesh<R> g(p);
-  Tally tl{0.0, 0.0, 0u};
+  Tally<R> tl{R(0), R(0), 0u, 0u};
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(wl.next, 1);
     __syncthreads();
@@ -390,9 +484,9 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
       if (c < 0) continue;
       const int i = c / nt, j = c - (c / nt) * nt;
       if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-        push_one<R>(m, p, s, q, tl);
+        push_one<R>(m, p, s, q, c, tl);
       else
-        push_one<R>(g, p, s, q, tl);
+        push_one_global<R>(p, s, q, c, tl);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < area; k += blockDim.x) {
@@ -405,7 +499,7 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
     }
     __syncthreads();
   }
-  flush_tally(tl, p.acc, p.status);
+  flush_tally(tl, p.acc, p.status, &p.pushed[0]);
 }
 
 template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo) {

@@ -53,7 +53,9 @@ class hff_info(C.Structure):
     _fields_ = [("dt", C.c_double), ("psi_unit", C.c_double), ("step", C.c_int64),
                 ("count", C.c_int64 * 4), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
                 ("sort_every", C.c_int32), ("precision", C.c_int32),
-                ("kernels_per_step", C.c_int64), ("kernels_launched", C.c_int64)]
+                ("kernels_per_step", C.c_int64), ("kernels_launched", C.c_int64),
+                ("pushed_tiled", C.c_int64), ("pushed_tail", C.c_int64),
+                ("readback_bytes", C.c_int64)]
 
 
 class hff_particle_view(C.Structure):
@@ -73,7 +75,7 @@ _lib = None
 
 # exported symbols (checked against include/hff.h by the tests)
 SYMBOLS = ["hff_plan", "hff_init", "hff_load_particles", "hff_set_field", "hff_fields", "hff_step",
-           "hff_step_stages", "hff_set_scalar", "hff_particles", "hff_diagnostics", "hff_get_info",
+           "hff_step_timed", "hff_step_stages", "hff_set_scalar", "hff_particles", "hff_diagnostics", "hff_get_info",
            "hff_status", "hff_destroy", "hff_last_error"]
 
 
@@ -93,6 +95,7 @@ def load(path: str = LIB_PATH):
         "hff_set_field": ([vp, C.c_int, C.c_int, vp, sz, C.c_int], C.c_int),
         "hff_fields": ([vp, C.c_int, C.c_int, vp, sz, C.c_int], C.c_int),
         "hff_step": ([vp, i32], C.c_int),
+        "hff_step_timed": ([vp, i32, vp, vp], C.c_int),
         "hff_step_stages": ([vp, i32, i32], C.c_int),
         "hff_set_scalar": ([vp, C.c_int, d], C.c_int),
         "hff_particles": ([vp, C.c_int, C.c_int, C.POINTER(hff_particle_view)], C.c_int),
@@ -175,6 +178,14 @@ def hff_fields(h, inst, which, dst_ptr, nbytes, where):
 
 def hff_step(h, nsteps: int):
     _check(load().hff_step(h, nsteps))
+
+
+def hff_step_timed(h, nsteps: int, ev_begin, ev_end):
+    """ev_begin / ev_end: sequences of nsteps cudaEvent_t handles (ints)."""
+    arr = C.c_void_p * max(1, nsteps)
+    b = arr(*[C.c_void_p(e) for e in ev_begin])
+    e = arr(*[C.c_void_p(x) for x in ev_end])
+    _check(load().hff_step_timed(h, nsteps, C.cast(b, C.c_void_p), C.cast(e, C.c_void_p)))
 
 
 def hff_step_stages(h, nsteps: int, stages: int):
@@ -293,6 +304,16 @@ class Sim:
 
     def step(self, n: int = 1) -> None:
         hff_step(self.h, n)
+
+    def step_timed(self, ev_begin, ev_end) -> None:
+        """One step per event pair (torch.cuda.Event with timing); the events
+        bracket the tiled push kernel.  Torch creates its CUDA events lazily,
+        so any event not yet created is recorded once here first."""
+        for e in list(ev_begin) + list(ev_end):
+            if not e.cuda_event:
+                e.record(self.stream)
+        hff_step_timed(self.h, len(ev_begin), [e.cuda_event for e in ev_begin],
+                       [e.cuda_event for e in ev_end])
 
     def step_stages(self, n: int, stages: int) -> None:
         hff_step_stages(self.h, n, stages)

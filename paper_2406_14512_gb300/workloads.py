@@ -94,6 +94,11 @@ def config(name: str) -> dict:
             c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=6000,
                      steps=10, precision="fp32", place="band", sheet_frac=0.2, momenta="powerlaw")
             c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
+        elif kind == "fine":     # hybrid, fine enough for the small-increment series (D, dtheta < 0.03)
+            c = _base(200, 120, 20.0, 4.0, "synth", seed=15)
+            c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=8000,
+                     steps=10, precision="fp32", place="band", sheet_frac=0.2, momenta="powerlaw")
+            c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
         elif kind == "michel":   # monopole, south hemisphere force-free (Sect. 4)
             c = _base(64, 64, 50.0 / 3.0, 5.0, "michel", seed=14)
             # sharp cut at the equator (Psi = Psi*), placed a hair below Psi* so
@@ -105,6 +110,21 @@ def config(name: str) -> dict:
     else:
         raise KeyError(name)
     return c
+
+
+def sample(name: str, n: int) -> dict:
+    """The workload `name` on an n x n grid with the same particles per cell
+    (a bounded sample for timing the CPU oracle)."""
+    c = config(name)
+    scale = (n * n) / float(c["nr"] * c["nt"])
+    small = _base(n, n, c["r_max"], c["r_lc"], c["geom"], kappa=c["kappa_inj"], seed=c["seed"])
+    for k in ("psi_break", "f_break", "precision", "place", "sheet_frac", "momenta", "steps"):
+        if k in c:
+            small[k] = c[k]
+    if c.get("gamma_rad", 0.0) > 0:
+        small["gamma_rad"] = 0.05 * (small["r_lc"] ** -2) / small["m"][0]
+    small["n_pairs"] = max(1, int(round(c["n_pairs"] * scale)))
+    return small
 
 
 # ---------------------------------------------------------------- particles

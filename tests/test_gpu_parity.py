@@ -65,7 +65,7 @@ def oracle_psi(ref):
 
 
 @pytest.mark.parametrize("name,prec,tol", [("small_pic", "fp64", 1e-10), ("small_hybrid", "fp32", 1e-5),
-                                           ("small_rr", "fp32", 1e-5)])
+                                           ("small_rr", "fp32", 1e-5), ("small_fine", "fp32", 1e-5)])
 def test_push_deposit_parity(env, name, prec, tol):
     """Gather, Boris + radiation reaction, move, kill rules and the
     charge-conserving deposit for one step in frozen fields."""
@@ -90,7 +90,8 @@ def test_push_deposit_parity(env, name, prec, tol):
             assert rel_l2(g[k][live], o[k][live]) < tol, k
 
 
-@pytest.mark.parametrize("name,prec", [("small_pic", "fp64"), ("small_hybrid", "fp32"), ("small_rr", "fp32")])
+@pytest.mark.parametrize("name,prec", [("small_pic", "fp64"), ("small_hybrid", "fp32"), ("small_rr", "fp32"),
+                                       ("small_fine", "fp32")])
 def test_ten_full_steps(env, name, prec):
     """Ten whole steps (graph path: tiled push, injection, sort every 4):
     particle order and cells identical up to face ties and positions within
