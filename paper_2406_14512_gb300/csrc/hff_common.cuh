@@ -71,6 +71,7 @@ struct Params {
   R dt, dlog, dth, omega, r_min, xi_abs, shell_r2;
   R inv_dlog, inv_dth;
   int small_grid;           // dlog and dtheta both below the series threshold
+  uint32_t div_m, div_s1, div_s2;  // cell / nt by multiplication (see decode_cell)
   int n_breaks;
   R psi_break[kMaxBreaks];  // absolute units
   R f_break[kMaxBreaks];
@@ -111,6 +112,17 @@ __device__ __forceinline__ R blend(const Params<R> &p, R psi) {
     }
   }
   return p.f_break[n - 1];
+}
+
+// cell = i * nt + j  ->  (i, j) with the division by the invariant nt done
+// as a multiply-high and shifts (Granlund & Montgomery 1994, unsigned
+// division by invariant integers: m = floor(2^32 (2^l - nt) / nt) + 1,
+// l = ceil(log2 nt), s1 = min(l, 1), s2 = max(l - 1, 0)).
+template <typename R>
+__device__ __forceinline__ void decode_cell(const Params<R> &p, int c, int &i, int &j) {
+  const uint32_t n = (uint32_t)c, t = __umulhi(p.div_m, n);
+  i = (int)((t + ((n - t) >> p.div_s1)) >> p.div_s2);
+  j = c - i * p.nt;
 }
 
 // row-major helpers (theta fastest)

@@ -31,9 +31,26 @@ struct GlobalMesh {
   __device__ __forceinline__ R bt(int i, int j) const { return p.f.bt[ix(i, j, p.nt + 1)]; }
   __device__ __forceinline__ R bp(int i, int j) const { return p.f.bp[ix(i, j, p.nt)]; }
   __device__ __forceinline__ bool ff(int i, int j) const { return p.f.ffcell[ix(i, j, p.nt)] != 0; }
-  __device__ __forceinline__ void add_jr(int i, int j, R v) const { atomicAdd(&p.f.jr[ix(i, j, p.nt + 1)], v); }
-  __device__ __forceinline__ void add_jt(int i, int j, R v) const { atomicAdd(&p.f.jt[ix(i, j, p.nt)], v); }
-  __device__ __forceinline__ void add_jp(int i, int j, R v) const { atomicAdd(&p.f.jp[ix(i, j, p.nt + 1)], v); }
+  // raw charge flux through a dual face (J_r, J_th) or charge x velocity at
+  // a node (J_ph), converted to a current density with the face area or
+  // node volume and dt here
+  // (indices outside the arrays carry zero flux for every valid move; they
+  // are still checked here, on the global path)
+  __device__ __forceinline__ void add_jr(int i, int j, R v) const {
+    if (i >= 0 && i < p.nr && j >= 0 && j <= p.nt)
+      atomicAdd(&p.f.jr[ix(i, j, p.nt + 1)], v * p.t.dep_r[i] * p.t.inv_dch[j]);
+  }
+  __device__ __forceinline__ void add_jt(int i, int j, R v) const {
+    if (i >= 0 && i <= p.nr && j >= 0 && j < p.nt)
+      atomicAdd(&p.f.jt[ix(i, j, p.nt)], v * p.t.dep_t[i] * p.t.inv_sh[j]);
+  }
+  __device__ __forceinline__ void add_jp(int i, int j, R v) const {
+    if (i >= 0 && i <= p.nr && j >= 0 && j <= p.nt)
+      atomicAdd(&p.f.jp[ix(i, j, p.nt + 1)], v * p.t.dep_p[i] * p.t.inv_dch[j]);
+  }
+  __device__ __forceinline__ R rn(int i) const { return p.t.rn[i]; }
+  __device__ __forceinline__ R sn(int j) const { return p.t.sn[j]; }
+  __device__ __forceinline__ R cn(int j) const { return p.t.cn[j]; }
 };
 
 // Shared-memory view of a tile region [i0, i0 + LR) x [j0, j0 + LT) of every
@@ -41,6 +58,7 @@ struct GlobalMesh {
 template <typename R>
 struct SharedMesh {
   R *s_er, *s_et, *s_ep, *s_br, *s_bt, *s_bp, *s_jr, *s_jt, *s_jp;
+  R *s_rn, *s_sn, *s_cn;   // row / column tables of the region
   uint8_t *s_ff;
   int i0, j0, lt;
   __device__ __forceinline__ int o(int i, int j) const { return (i - i0) * lt + (j - j0); }
@@ -54,6 +72,9 @@ struct SharedMesh {
   __device__ __forceinline__ void add_jr(int i, int j, R v) const { atomicAdd(&s_jr[o(i, j)], v); }
   __device__ __forceinline__ void add_jt(int i, int j, R v) const { atomicAdd(&s_jt[o(i, j)], v); }
   __device__ __forceinline__ void add_jp(int i, int j, R v) const { atomicAdd(&s_jp[o(i, j)], v); }
+  __device__ __forceinline__ R rn(int i) const { return s_rn[i - i0]; }
+  __device__ __forceinline__ R sn(int j) const { return s_sn[j - j0]; }
+  __device__ __forceinline__ R cn(int j) const { return s_cn[j - j0]; }
 };
 
 // 1D linear weights for a component at positions k + a (a = 0 or 1/2),
@@ -92,28 +113,33 @@ template <typename R> __device__ __forceinline__ R exp_small(R x) {
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 template <typename R, typename M, typename Get>
 __device__ __forceinline__ R interp(const M &m, Get g, int i, R wi, int j, R wj) {
-  return (R(1) - wi) * ((R(1) - wj) * g(m, i, j) + wj * g(m, i, j + 1)) +
-         wi * ((R(1) - wj) * g(m, i + 1, j) + wj * g(m, i + 1, j + 1));
+  const R a0 = g(m, i, j), a1 = g(m, i, j + 1), b0 = g(m, i + 1, j), b1 = g(m, i + 1, j + 1);
+  const R lo = a0 + wj * (a1 - a0), hi = b0 + wj * (b1 - b0);
+  return lo + wi * (hi - lo);
 }
 
 template <typename R, typename M>
 __device__ __forceinline__ void gather(const M &m, int nr, int nt, int i, int j, R xo, R yo, R e[3], R b[3]) {
-  int ki, kj;
-  R wi, wj;
-  stag(i, xo, true, nr, ki, wi); stag(j, yo, false, nt + 1, kj, wj);
-  e[0] = interp(m, [](const M &q, int a, int c) { return q.er(a, c); }, ki, wi, kj, wj);
-  b[1] = interp(m, [](const M &q, int a, int c) { return q.bt(a, c); }, ki, wi, kj, wj);
-  stag(i, xo, false, nr + 1, ki, wi); stag(j, yo, true, nt, kj, wj);
-  e[1] = interp(m, [](const M &q, int a, int c) { return q.et(a, c); }, ki, wi, kj, wj);
-  b[0] = interp(m, [](const M &q, int a, int c) { return q.br(a, c); }, ki, wi, kj, wj);
-  stag(i, xo, false, nr + 1, ki, wi); stag(j, yo, false, nt + 1, kj, wj);
-  e[2] = interp(m, [](const M &q, int a, int c) { return q.ep(a, c); }, ki, wi, kj, wj);
-  stag(i, xo, true, nr, ki, wi); stag(j, yo, true, nt, kj, wj);
-  b[2] = interp(m, [](const M &q, int a, int c) { return q.bp(a, c); }, ki, wi, kj, wj);
+  // the four (node | half) x (node | half) weight sets, each shared by the
+  // components that live there
+  int kin, kih, kjn, kjh;
+  R win, wih, wjn, wjh;
+  stag(i, xo, false, nr + 1, kin, win);
+  stag(i, xo, true, nr, kih, wih);
+  stag(j, yo, false, nt + 1, kjn, wjn);
+  stag(j, yo, true, nt, kjh, wjh);
+  e[0] = interp(m, [](const M &q, int a, int c) { return q.er(a, c); }, kih, wih, kjn, wjn);
+  b[1] = interp(m, [](const M &q, int a, int c) { return q.bt(a, c); }, kih, wih, kjn, wjn);
+  e[1] = interp(m, [](const M &q, int a, int c) { return q.et(a, c); }, kin, win, kjh, wjh);
+  b[0] = interp(m, [](const M &q, int a, int c) { return q.br(a, c); }, kin, win, kjh, wjh);
+  e[2] = interp(m, [](const M &q, int a, int c) { return q.ep(a, c); }, kin, win, kjn, wjn);
+  b[2] = interp(m, [](const M &q, int a, int c) { return q.bp(a, c); }, kih, wih, kjh, wjh);
 }
 
 // Modified Boris step (Eqs. 15-17, c = 1): Lorentz Boris gives u_L, the
@@ -128,7 +154,7 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
   const R um0 = u[0] + a * e[0], um1 = u[1] + a * e[1], um2 = u[2] + a * e[2];
   const R ig = rsq(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
   const R t0 = a * b[0] * ig, t1 = a * b[1] * ig, t2 = a * b[2] * ig;
-  const R sc = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
+  const R sc = R(2) * rcp(R(1) + t0 * t0 + t1 * t1 + t2 * t2);
   const R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;
   const R v0 = um0 + (um1 * t2 - um2 * t1), v1 = um1 + (um2 * t0 - um0 * t2), v2 = um2 + (um0 * t1 - um1 * t0);
   const R ul0 = um0 + (v1 * s2 - v2 * s1) + a * e[0];
@@ -153,7 +179,7 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
     const R du1 = k * ((f2 * b[0] - f0 * b[2]) + bdot * e[1] - g2 * bp2 * be1);
     const R du2 = k * ((f0 * b[1] - f1 * b[0]) + bdot * e[2] - g2 * bp2 * be2);
     const R dn2 = du0 * du0 + du1 * du1 + du2 * du2, ul2s = ul0 * ul0 + ul1 * ul1 + ul2 * ul2;
-    const R lim = (dn2 > R(0.25) * ul2s) ? R(0.5) * sqrt(ul2s / dn2) : R(1);
+    const R lim = (dn2 > R(0.25) * ul2s) ? R(0.5) * sqrt(ul2s * rcp(dn2)) : R(1);
     out[0] = ul0 + lim * du0;
     out[1] = ul1 + lim * du1;
     out[2] = ul2 + lim * du2;
@@ -204,14 +230,14 @@ __device__ __forceinline__ bool move_small(R r, R sn, R cs, R dt, const R u[3], 
   const R x = (r + d0) * sn + d1 * cs;
   if (!(x > R(0)) || fabs(d2) >= R(kSmall) * x) return false;
   const R tp = fdiv(d2, x), qp = tp * tp;
-  const R sqp = sqrt(R(1) + qp), cp = R(1) / sqp;
+  const R cp = rsq(R(1) + qp), sqp = (R(1) + qp) * cp;
   const R sp = tp * cp, omc = qp / (sqp * (sqp + R(1)));  // 1 - cos(phi)
   const R dR = x * omc * sqp;                                // sqrt(x^2+d2^2) - x
   const R pa = d0 + dR * sn;
   const R a = r + pa, bb = d1 + dR * cs;
   if (fabs(bb) >= R(kSmall) * a) return false;
   const R ta = fdiv(bb, a), qa = ta * ta;
-  const R sqa = sqrt(R(1) + qa), ca = R(1) / sqa, sa = ta * ca;
+  const R ca = rsq(R(1) + qa), sqa = (R(1) + qa) * ca, sa = ta * ca;
   const R rnew = a * sqa;
   dr = fdiv(pa * (R(2) * r + pa) + bb * bb, rnew + r);
   dth = atan_small(ta);
@@ -225,86 +251,83 @@ __device__ __forceinline__ bool move_small(R r, R sn, R cs, R dt, const R u[3], 
 }
 
 // Charge-conserving deposit for linear shapes (Esirkepov decomposition) in
-// the logical (xi, eta) plane: charge through each dual face over the exact
-// face area and dt gives J_r, J_th; J_ph uses mid-point weights over the
-// node dual volume.  (x0, y0) in [0,1) is the start offset in cell (i0, j0);
-// (X1, Y1) the end point relative to node (i0, j0), in (-1, 2).  The four
-// stencil weights per direction are formed with selects (no indexed arrays),
-// and for a move inside one cell the weight change is +-(X1 - x0) exactly.
+// the logical (xi, eta) plane.  (x0, y0) in [0,1) is the start offset in cell
+// (i0, j0) and (X1, Y1) the end point relative to node (i0, j0), in (-1, 2).
+// With S0, S1 the start and end weights on the nodes i0-1 .. i0+2 and
+// dS = S1 - S0, the charge through the radial dual face between nodes a and
+// a+1 in row b is -q (dS_x[0] + .. + dS_x[a]) (S0_y[b] + S1_y[b]) / 2, and
+// likewise in theta; J_ph uses the mid-point weights.  For linear weights the
+// nonzero radial fluxes always lie in a 2-face x 3-row window (and the polar
+// ones in a 3 x 2 window) placed by the direction of any cell crossing, so
+// every particle runs the same 16 predicated updates, with no data-dependent
+// loops.  The accessor receives raw charge fluxes (charge x velocity for
+// J_ph); the face areas, node volumes and dt are applied where the flux
+// reaches global memory.
 template <typename R>
-__device__ __forceinline__ void shape_delta(R x0, R X1, R s1[4], R ds[4], R sum[4]) {
-  const int k = (X1 < R(0)) ? -1 : (X1 < R(1) ? 0 : 1);
-  s1[0] = (k < 0) ? -X1 : R(0);
-  s1[1] = (k < 0) ? R(1) + X1 : (k == 0 ? R(1) - X1 : R(0));
-  s1[2] = (k == 0) ? X1 : (k > 0 ? R(2) - X1 : R(0));
-  s1[3] = (k > 0) ? X1 - R(1) : R(0);
-  if (k == 0) {
-    const R d = X1 - x0;
-    ds[0] = R(0); ds[1] = -d; ds[2] = d; ds[3] = R(0);
-  } else {
-    ds[0] = s1[0]; ds[1] = s1[1] - (R(1) - x0); ds[2] = s1[2] - x0; ds[3] = s1[3];
-  }
-  sum[0] = R(0.5) * s1[0];
-  sum[1] = R(0.5) * (s1[1] + (R(1) - x0));
-  sum[2] = R(0.5) * (s1[2] + x0);
-  sum[3] = R(0.5) * s1[3];
+struct Axis {  // weights along one direction
+  R f0, f1;       // prefix-summed dS on the two faces of the window
+  R m0, m1, m2;   // (S0 + S1) / 2 on the three nodes of the window
+  int a0;         // window start relative to node i0 - 1 (0 or 1)
+};
+
+template <typename R>
+__device__ __forceinline__ Axis<R> axis_weights(R x0, R X1) {
+  Axis<R> w;
+  const bool lo = X1 < R(0), hi = X1 >= R(1);
+  // end weights on the nodes -1, 0, 1, 2 (relative to the start node)
+  const R e0 = lo ? -X1 : R(0);
+  const R e1 = lo ? R(1) + X1 : (hi ? R(0) : R(1) - X1);
+  const R e2 = lo ? R(0) : (hi ? R(2) - X1 : X1);
+  const R e3 = hi ? X1 - R(1) : R(0);
+  // prefix sums of dS = e - (0, 1 - x0, x0, 0) on the faces -1/2, 1/2, 3/2;
+  // inside one cell the middle one is -(X1 - x0) exactly
+  const R p0 = e0;
+  const R p1 = (lo || hi) ? e0 + e1 - (R(1) - x0) : x0 - X1;
+  const R p2 = hi ? p1 + e2 - x0 : R(0);  // zero without a crossing (exactly)
+  // weights (S0 + S1)/2 on the nodes -1 .. 2
+  const R n0 = R(0.5) * e0, n1 = R(0.5) * (e1 + R(1) - x0), n2 = R(0.5) * (e2 + x0), n3 = R(0.5) * e3;
+  w.a0 = lo ? 0 : 1;
+  w.f0 = lo ? p0 : p1;
+  w.f1 = lo ? p1 : p2;
+  w.m0 = lo ? n0 : n1;
+  w.m1 = lo ? n1 : n2;
+  w.m2 = lo ? n2 : n3;
+  return w;
 }
 
 template <typename R, typename M>
-__device__ __forceinline__ void deposit(const M &m, const Params<R> &p, R qw, int i0, int j0, R x0, R y0,
-                                        R X1, R Y1, R vphi) {
-  const int nr = p.nr, nt = p.nt;
-  R s1x[4], dsx[4], mx[4], s1y[4], dsy[4], my[4];
-  shape_delta(x0, X1, s1x, dsx, mx);
-  shape_delta(y0, Y1, s1y, dsy, my);
-  const Tables<R> &t = p.t;
+__device__ __forceinline__ void deposit(const M &m, R qw, int i0, int j0, R x0, R y0, R X1, R Y1, R vphi) {
+  const Axis<R> ax = axis_weights(x0, X1), ay = axis_weights(y0, Y1);
   const R nq = -qw;
-  R ax[3];
-  ax[0] = dsx[0]; ax[1] = ax[0] + dsx[1]; ax[2] = ax[1] + dsx[2];
+  const int ib = i0 - 1 + ax.a0, jb = j0 - 1 + ay.a0;
+  // radial faces ib, ib+1 (E_r rows) x nodes jb .. jb+2
+  {
+    const R g0 = nq * ax.f0, g1 = nq * ax.f1;
+    const R v[6] = {g0 * ay.m0, g0 * ay.m1, g0 * ay.m2, g1 * ay.m0, g1 * ay.m1, g1 * ay.m2};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (ax[a] == R(0)) continue;
-    const int ii = i0 - 1 + a;
-    if (ii < 0 || ii >= nr) continue;
-    const R f = nq * ax[a] * t.dep_r[ii];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int jj = j0 - 1 + b;
-      if (my[b] != R(0) && jj >= 0 && jj <= nt) m.add_jr(ii, jj, f * my[b] * t.inv_dch[jj]);
-    }
+    for (int k = 0; k < 6; ++k)
+      if (v[k] != R(0)) m.add_jr(ib + k / 3, jb + k % 3, v[k]);
   }
-  R ay[3];
-  ay[0] = dsy[0]; ay[1] = ay[0] + dsy[1]; ay[2] = ay[1] + dsy[2];
+  // polar faces jb, jb+1 (E_th columns) x nodes ib .. ib+2
+  {
+    const R g0 = nq * ay.f0, g1 = nq * ay.f1;
+    const R v[6] = {g0 * ax.m0, g0 * ax.m1, g0 * ax.m2, g1 * ax.m0, g1 * ax.m1, g1 * ax.m2};
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    if (ay[b] == R(0)) continue;
-    const int jj = j0 - 1 + b;
-    if (jj < 0 || jj >= nt) continue;
-    const R f = nq * ay[b] * t.inv_sh[jj];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int ii = i0 - 1 + a;
-      if (mx[a] != R(0) && ii >= 0 && ii <= nr) m.add_jt(ii, jj, f * mx[a] * t.dep_t[ii]);
-    }
+    for (int k = 0; k < 6; ++k)
+      if (v[k] != R(0)) m.add_jt(ib + k % 3, jb + k / 3, v[k]);
   }
-  if (vphi != R(0)) {
+  // J_ph at the mid-point
+  {
     const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
     const int km = (xm < R(0)) ? -1 : (xm < R(1) ? 0 : 1);
     const int lm = (ym < R(0)) ? -1 : (ym < R(1) ? 0 : 1);
     const R wx = xm - R(km), wy = ym - R(lm);
     const R qv = qw * vphi;
+    const R a0 = qv * (R(1) - wx), a1 = qv * wx;
+    const R v[4] = {a0 * (R(1) - wy), a0 * wy, a1 * (R(1) - wy), a1 * wy};
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int ii = i0 + km + a;
-      if (ii < 0 || ii > nr) continue;
-      const R fa = qv * (a ? wx : R(1) - wx) * t.dep_p[ii];
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int jj = j0 + lm + b;
-        const R wg = (b ? wy : R(1) - wy);
-        if (wg != R(0) && fa != R(0) && jj >= 0 && jj <= nt) m.add_jp(ii, jj, fa * wg * t.inv_dch[jj]);
-      }
-    }
+    for (int k = 0; k < 4; ++k)
+      if (v[k] != R(0)) m.add_jp(i0 + km + k / 2, j0 + lm + k % 2, v[k]);
   }
 }
 
@@ -321,20 +344,28 @@ struct Tally {
   unsigned pushed;
 };
 
+// per-species constants of a push, loaded once per work item
+template <typename R>
+struct SpeciesConst {
+  Species<R> S;
+  R qm, krr, q, m;
+  __device__ __forceinline__ SpeciesConst(const Params<R> &p, int s)
+      : S(p.sp[s]), qm(p.qm[s]), krr(p.krr[s] * (R)(*p.rr_scale)), q(p.q[s]), m(p.m[s]) {}
+};
+
 // One particle: gather, push, move, kill rules, deposit, store.
 template <typename R, typename M>
-__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, int64_t q, int c, Tally<R> &tl) {
-  const Species<R> &S = p.sp[s];
+__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const SpeciesConst<R> &K, int64_t q,
+                                         int i, int j, Tally<R> &tl) {
+  const Species<R> &S = K.S;
   const int nt = p.nt, nr = p.nr;
-  const int i = c / nt, j = c - i * nt;
   const R xo = S.xo[q], yo = S.yo[q], w = S.w[q];
   R u[3] = {S.ur[q], S.ut[q], S.up[q]};
   R e[3], b[3], un[3], dg;
   tl.pushed += 1;
   gather<R>(m, nr, nt, i, j, xo, yo, e, b);
-  const R krr = p.krr[s] * (R)(*p.rr_scale);
-  boris_rr<R>(p.qm[s], krr, p.dt, u, e, b, un, dg);
-  tl.radiated += w * p.m[s] * dg;
+  boris_rr<R>(K.qm, K.krr, p.dt, u, e, b, un, dg);
+  tl.radiated += w * K.m * dg;
   // position of the particle: r = r_i exp(xo D), theta = theta_j + yo dtheta
   const R xl = xo * p.dlog, ya = yo * p.dth;
   R ex, sa0, ca0;
@@ -346,19 +377,20 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
     ex = exp(xl);
     sincos(ya, &sa0, &ca0);
   }
-  const R r = p.t.rn[i] * ex;
-  const R sn = p.t.sn[j] * ca0 + p.t.cn[j] * sa0, cs = p.t.cn[j] * ca0 - p.t.sn[j] * sa0;
+  const R r = m.rn(i) * ex;
+  const R snj = m.sn(j), cnj = m.cn(j);
+  const R sn = snj * ca0 + cnj * sa0, cs = cnj * ca0 - snj * sa0;
   if (r * r < p.shell_r2) {  // Sect. 5.1: no momentum across B near the star
     const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
     if (b2 > R(1e-30)) {
-      const R ub = (un[0] * b[0] + un[1] * b[1] + un[2] * b[2]) / b2;
+      const R ub = (un[0] * b[0] + un[1] * b[1] + un[2] * b[2]) * rcp(b2);
       un[0] = ub * b[0]; un[1] = ub * b[1]; un[2] = ub * b[2];
     }
   }
   R dr, dth, uo[3];
   if (!move_small<R>(r, sn, cs, p.dt, un, dr, dth, uo)) move_general<R>(r, sn, cs, p.dt, un, dr, dth, uo);
   const R ginv = rsq(R(1) + un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
-  const R xr = dr / r;
+  const R xr = dr * rcp(r);
   R X1 = xo + ((fabs(xr) < R(kSmall)) ? log1p_small(xr) : log1p(xr)) * p.inv_dlog;
   R Y1 = yo + dth * p.inv_dth;
   if (!isfinite(X1) || !isfinite(Y1) || !isfinite(uo[0] + uo[1] + uo[2])) {
@@ -379,7 +411,7 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
   int j1 = j + dj;
   if (j1 >= nt) { j1 = nt - 1; yn = one_minus_ulp<R>(); }
   if (!dead && m.ff(i1, j1)) dead = true;
-  deposit<R>(m, p, p.q[s] * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
+  deposit<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
   if (dead) {
     S.cell[q] = -1;
     tl.killed += w;
@@ -394,9 +426,10 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, int s, 
 // out-of-region fallback of the tiled kernel (kept out of line so that the
 // hot loop stays small)
 template <typename R>
-__device__ __noinline__ void push_one_global(const Params<R> &p, int s, int64_t q, int c, Tally<R> &tl) {
+__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int64_t q, int i, int j,
+                                             Tally<R> &tl) {
   GlobalMesh<R> g(p);
-  push_one<R>(g, p, s, q, c, tl);
+  push_one<R>(g, p, K, q, i, j, tl);
 }
 
 template <typename R>
@@ -424,11 +457,15 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
   GlobalMesh<R> m(p);
   Tally<R> tl{R(0), R(0), 0u, 0u};
   for (int s = 0; s < p.n_species; ++s) {
+    const SpeciesConst<R> K(p, s);
     const int64_t n0 = p.count_sorted[s], n1 = p.count[s];
     for (int64_t q = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n1;
          q += (int64_t)gridDim.x * blockDim.x) {
       const int c = p.sp[s].cell[q];
-      if (c >= 0) push_one<R>(m, p, s, q, c, tl);
+      if (c < 0) continue;
+      int i, j;
+      decode_cell(p, c, i, j);
+      push_one<R>(m, p, K, q, i, j, tl);
     }
   }
   flush_tally(tl, p.acc, p.status, &p.pushed[1]);
@@ -438,7 +475,7 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
 // Region of a tile: cells [ti*TR - H, (ti+1)*TR + H) (and likewise in theta)
 // widened by the stencil: one node below, two above.
 template <typename R>
-__global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, int halo) {
+__global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl, int halo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
   R *base = reinterpret_cast<R *>(smem);
@@ -446,7 +483,8 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
   m.s_er = base; m.s_et = base + area; m.s_ep = base + 2 * area;
   m.s_br = base + 3 * area; m.s_bt = base + 4 * area; m.s_bp = base + 5 * area;
   m.s_jr = base + 6 * area; m.s_jt = base + 7 * area; m.s_jp = base + 8 * area;
-  m.s_ff = reinterpret_cast<uint8_t *>(base + 9 * area);
+  m.s_rn = base + 9 * area; m.s_sn = m.s_rn + lr; m.s_cn = m.s_sn + lt;
+  m.s_ff = reinterpret_cast<uint8_t *>(m.s_cn + lt);
   m.lt = lt;
   __shared__ int s_item;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
@@ -475,6 +513,16 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
       m.s_ff[k] = (okr && okj && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
       m.s_jr[k] = R(0); m.s_jt[k] = R(0); m.s_jp[k] = R(0);
     }
+    for (int k = threadIdx.x; k < lr; k += blockDim.x) {
+      const int gi = m.i0 + k;
+      m.s_rn[k] = (gi >= 0 && gi <= nr) ? p.t.rn[gi] : R(1);
+    }
+    for (int k = threadIdx.x; k < lt; k += blockDim.x) {
+      const int gj = m.j0 + k;
+      m.s_sn[k] = (gj >= 0 && gj <= nt) ? p.t.sn[gj] : R(0);
+      m.s_cn[k] = (gj >= 0 && gj <= nt) ? p.t.cn[gj] : R(1);
+    }
+    const SpeciesConst<R> K(p, s);
     __syncthreads();
     const int64_t q0 = item.z, q1 = (int64_t)item.z + item.w;
     // a particle is handled in shared memory when its whole stencil (start
@@ -482,20 +530,25 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
     for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
       const int c = p.sp[s].cell[q];
       if (c < 0) continue;
-      const int i = c / nt, j = c - (c / nt) * nt;
+      int i, j;
+      decode_cell(p, c, i, j);
       if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-        push_one<R>(m, p, s, q, c, tl);
+        push_one<R>(m, p, K, q, i, j, tl);
       else
-        push_one_global<R>(p, s, q, c, tl);
+        push_one_global<R>(p, K, q, i, j, tl);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < area; k += blockDim.x) {
       const int a = k / lt, c = k - a * lt;
       const int gi = m.i0 + a, gj = m.j0 + c;
       if (gi < 0 || gj < 0) continue;
-      if (m.s_jr[k] != R(0) && gi < nr && gj <= nt) atomicAdd(&p.f.jr[ix(gi, gj, n1)], m.s_jr[k]);
-      if (m.s_jt[k] != R(0) && gi <= nr && gj < nt) atomicAdd(&p.f.jt[ix(gi, gj, nt)], m.s_jt[k]);
-      if (m.s_jp[k] != R(0) && gi <= nr && gj <= nt) atomicAdd(&p.f.jp[ix(gi, gj, n1)], m.s_jp[k]);
+      // raw fluxes -> current densities (face areas, node volumes, dt)
+      if (m.s_jr[k] != R(0) && gi < nr && gj <= nt)
+        atomicAdd(&p.f.jr[ix(gi, gj, n1)], m.s_jr[k] * p.t.dep_r[gi] * p.t.inv_dch[gj]);
+      if (m.s_jt[k] != R(0) && gi <= nr && gj < nt)
+        atomicAdd(&p.f.jt[ix(gi, gj, nt)], m.s_jt[k] * p.t.dep_t[gi] * p.t.inv_sh[gj]);
+      if (m.s_jp[k] != R(0) && gi <= nr && gj <= nt)
+        atomicAdd(&p.f.jp[ix(gi, gj, n1)], m.s_jp[k] * p.t.dep_p[gi] * p.t.inv_dch[gj]);
     }
     __syncthreads();
   }
@@ -503,8 +556,8 @@ __global__ void __launch_bounds__(256) k_push_tiled(Params<R> p, WorkList wl, in
 }
 
 template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo) {
-  const size_t area = (size_t)(p.tile_r + 2 * halo + 4) * (p.tile_t + 2 * halo + 4);
-  return area * (9 * sizeof(R) + 1);
+  const size_t lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
+  return area * (9 * sizeof(R) + 1) + (lr + 2 * lt) * sizeof(R);
 }
 
 template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, int grid) {
