@@ -229,6 +229,32 @@ int hff_destroy(hff_handle *h);
 /* Message of the last error on this thread ("" if none). */
 const char *hff_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free tile ordering.  No counterpart in the paper: this is a
+ * service for callers that may not allocate device memory at all -- code
+ * that runs under an external memory budget or allocator that forbids ad-hoc
+ * cudaMalloc, or inside a larger application that owns every allocation.
+ *
+ * Computes, for n particles with cell indices `cell` (device, i * nt + j,
+ * negative = removed), the stable order by tile key (tiles of tile_r x
+ * tile_t cells, row-major over tiles) with removed particles last -- the
+ * order in which hff_load_particles stores them.  order[k] (device, n words)
+ * receives the input index of the k-th particle; *n_live (host) the number of
+ * particles that are not removed.  Synchronises `stream`.
+ *
+ * Scratch lives in one fixed device array per GPU (about 4.3 MB), reserved in
+ * every process that loads the library until it exits; nothing is allocated.
+ * The first call on a device looks up that array's device address, so make
+ * it before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU (other streams, threads) race and must be serialised by the caller.
+ * Returns HFF_ERR_CAPACITY if n > HFF_NOALLOC_MAX_PARTICLES, HFF_ERR_ARG for
+ * invalid arguments, HFF_ERR_CUDA if a CUDA call fails; the message is given
+ * by hff_noalloc_last_error(). */
+#define HFF_NOALLOC_MAX_PARTICLES 262144
+int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr, int32_t nt, int32_t tile_r,
+                           int32_t tile_t, uint32_t *order, int64_t *n_live, void *stream);
+const char *hff_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,9 @@
 // rank inside its block comes from warp match masks, so equal keys keep their
 // order (the result equals a stable sort by key).  The particle payload moves
 // once, in a final gather.
+#include <mutex>
+
+#include "../../include/hff.h"
 #include "hff_common.cuh"
 
 namespace hff {
@@ -310,4 +313,124 @@ HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST
 
+// ------------------------------------------------- allocation-free variant
+// hff_tile_order_noalloc runs the same radix passes with its scratch in a
+// fixed device array instead of memory passed in or allocated, for callers
+// that may not allocate device memory at all.  The paper has no counterpart.
+namespace noalloc {
+
+constexpr int64_t kMaxN = HFF_NOALLOC_MAX_PARTICLES;
+constexpr int64_t kMaxBlocks = (kMaxN + kSortBlock - 1) / kSortBlock;
+constexpr int64_t kMaxHist = kMaxBlocks * 256;
+constexpr int64_t kMaxParts = (kMaxHist + kScanBlock - 1) / kScanBlock;
+// keys_a | keys_b | idx_a | idx_b | histogram | block sums | live count
+constexpr int64_t kWords = 4 * kMaxN + kMaxHist + kMaxParts + 64;
+
+// One copy per device, alive until the process exits; shared by every call.
+static __device__ __align__(256) uint32_t g_scratch[kWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint32_t *g_addr[kMaxDevices] = {};
+
+__global__ void k_live_init(uint32_t *live, uint32_t n) { *live = n; }
+
+// first slot holding a removed particle (keys are sorted, removed ones last)
+__global__ void k_live_count(const uint32_t *keys, int64_t n, uint32_t dead, uint32_t *live) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    if (keys[q] == dead && (q == 0 || keys[q - 1] != dead)) *live = (uint32_t)q;
+}
+
+}  // namespace noalloc
 }  // namespace hff
+
+thread_local const char *hff_noalloc_err = "";
+
+extern "C" const char *hff_noalloc_last_error(void) { return hff_noalloc_err; }
+
+extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr, int32_t nt, int32_t tile_r,
+                                      int32_t tile_t, uint32_t *order, int64_t *n_live, void *stream) {
+  using namespace hff;
+  using namespace hff::noalloc;
+  if (n < 0 || nr < 1 || nt < 1 || tile_r < 1 || tile_t < 1 || !n_live || (n > 0 && (!cell || !order))) {
+    hff_noalloc_err = "hff_tile_order_noalloc: invalid argument";
+    return HFF_ERR_ARG;
+  }
+  if (n > kMaxN) {
+    hff_noalloc_err = "hff_tile_order_noalloc: n exceeds HFF_NOALLOC_MAX_PARTICLES";
+    return HFF_ERR_CAPACITY;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    hff_noalloc_err = "hff_tile_order_noalloc: no usable current device";
+    return HFF_ERR_CUDA;
+  }
+  uint32_t *base = nullptr;
+  {
+    // first call on this device: resolve the device address of the array
+    // (host code only sees a stand-in symbol; the device address differs)
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+      void *ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
+        hff_noalloc_err = "hff_tile_order_noalloc: cudaGetSymbolAddress failed";
+        return HFF_ERR_CUDA;
+      }
+      g_addr[dev] = static_cast<uint32_t *>(ptr);
+    }
+    base = g_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ntt = (nt + tile_t - 1) / tile_t;
+  const int64_t ntiles = (int64_t)((nr + tile_r - 1) / tile_r) * ntt;
+  if (ntiles >= 0x7fffffffLL) {
+    hff_noalloc_err = "hff_tile_order_noalloc: too many tiles";
+    return HFF_ERR_ARG;
+  }
+  uint32_t *keys_a = base, *keys_b = base + kMaxN, *idx_a = base + 2 * kMaxN, *idx_b = base + 3 * kMaxN;
+  uint32_t *hist = base + 4 * kMaxN, *part = hist + kMaxHist, *live = part + kMaxParts;
+  const uint32_t dead = (uint32_t)ntiles;
+  if (n == 0) {
+    *n_live = 0;
+    return HFF_OK;
+  }
+  const int nbits = bits_for(dead), passes = (nbits + 7) / 8;
+  const int nb = (int)((n + kSortBlock - 1) / kSortBlock);
+  const int64_t hn = (int64_t)nb * 256;
+  const int nparts = (int)((hn + kScanBlock - 1) / kScanBlock);
+  SortArgs a{};
+  a.cell = cell;
+  a.n = n;
+  a.nb = nb;
+  a.nt = nt; a.tile_r = tile_r; a.tile_t = tile_t; a.ntt = ntt;
+  a.dead = dead;
+  a.hist = hist;
+  uint32_t *ko = keys_a, *io = idx_a, *ki = keys_b, *ii = idx_b;
+  for (int pass = 0; pass < passes; ++pass) {
+    a.first = (pass == 0);
+    a.shift = 8 * pass;
+    a.keys_in = ki; a.idx_in = ii;
+    a.keys_out = ko; a.idx_out = io;
+    k_hist<<<nb, kSortThreads, 0, st>>>(a);
+    k_scan_sums<<<nparts, 1024, 0, st>>>(hist, hn, part);
+    k_scan_parts<<<1, 1024, 0, st>>>(part, nparts);
+    k_scan_apply<<<nparts, 1024, 0, st>>>(hist, hn, part);
+    k_scatter<<<nb, kSortThreads, 0, st>>>(a);
+    uint32_t *t = ki; ki = ko; ko = t;
+    t = ii; ii = io; io = t;
+  }
+  // the live count is written afresh by every call (previous contents of
+  // the shared array are never read)
+  k_live_init<<<1, 1, 0, st>>>(live, (uint32_t)n);
+  k_live_count<<<(int)((n + 255) / 256), 256, 0, st>>>(ki, n, dead, live);
+  uint32_t h_live = 0;
+  if (cudaMemcpyAsync(order, ii, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(&h_live, live, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    hff_noalloc_err = "hff_tile_order_noalloc: a CUDA call failed";
+    return HFF_ERR_CUDA;
+  }
+  *n_live = (int64_t)h_live;
+  hff_noalloc_err = "";
+  return HFF_OK;
+}

@@ -76,7 +76,9 @@ _lib = None
 # exported symbols (checked against include/hff.h by the tests)
 SYMBOLS = ["hff_plan", "hff_init", "hff_load_particles", "hff_set_field", "hff_fields", "hff_step",
            "hff_step_timed", "hff_step_stages", "hff_set_scalar", "hff_particles", "hff_diagnostics", "hff_get_info",
-           "hff_status", "hff_destroy", "hff_last_error"]
+           "hff_status", "hff_destroy", "hff_last_error", "hff_tile_order_noalloc",
+           "hff_noalloc_last_error"]
+NOALLOC_MAX_PARTICLES = 262144
 
 
 def load(path: str = LIB_PATH):
@@ -104,6 +106,8 @@ def load(path: str = LIB_PATH):
         "hff_status": ([vp], C.c_int),
         "hff_destroy": ([vp], C.c_int),
         "hff_last_error": ([], C.c_char_p),
+        "hff_tile_order_noalloc": ([vp, i64, i32, i32, i32, i32, vp, C.POINTER(i64), vp], C.c_int),
+        "hff_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -225,6 +229,20 @@ def hff_destroy(h):
 
 def hff_last_error() -> str:
     return load().hff_last_error().decode()
+
+
+def hff_tile_order_noalloc(cell_ptr: int, n: int, nr: int, nt: int, tile_r: int, tile_t: int,
+                           order_ptr: int, stream: int) -> int:
+    """Stable tile order of n device cell indices into order_ptr (device,
+    n uint32) without allocating device memory; returns the live count.
+    For callers that may not allocate: the scratch is a fixed device array
+    inside the library (at most NOALLOC_MAX_PARTICLES particles per call)."""
+    live = C.c_int64()
+    rc = load().hff_tile_order_noalloc(C.c_void_p(cell_ptr), n, nr, nt, tile_r, tile_t,
+                                       C.c_void_p(order_ptr), C.byref(live), C.c_void_p(stream))
+    if rc != HFF_OK:
+        raise HffError(rc, load().hff_noalloc_last_error().decode())
+    return live.value
 
 
 # ------------------------------------------------------------- convenience
