@@ -1,0 +1,102 @@
+"""Parity at the full size of the benchmark workload (4096 x 4096 grid, 3e8
+e+-, FP32, tiles 16 x 32, sort every 8 steps), in the launch configuration
+that bench.py times.
+
+The oracle cannot push 3e8 particles in a test, so it is given every particle
+that starts in a band of rows; the current those particles deposit is then
+complete on the inner rows of the band, and is compared element by element
+with the GPU's; their new states are compared one by one.  The sort of all
+3e8 particles is checked bit-exactly against numpy's stable sort of the same
+keys, and div B = 0 after a whole step on the GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import particle_mismatches, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255)
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_14512_gb300 import hff, workloads
+    cfg = workloads.config("c3")
+    cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
+    ps = workloads.particles(cfg, threads=16)
+    sim = hff.Sim(cfg)
+    for s in range(2):
+        sim.load(s, ps[s])
+    return cfg, ps, sim
+
+
+def tile_keys(cell, cfg):
+    nt = cfg["nt"]
+    ntt = (nt + cfg["tile_t"] - 1) // cfg["tile_t"]
+    i, j = cell // nt, cell % nt
+    return (i // cfg["tile_r"]) * ntt + j // cfg["tile_t"]
+
+
+def test_fullsize_sort_is_stable_tile_order(full):
+    cfg, ps, sim = full
+    for s in range(2):
+        g = sim.particles(s)["cell"]
+        cell = ps[s]["cell"]
+        order = np.argsort(tile_keys(cell.astype(np.int64), cfg), kind="stable")
+        assert np.array_equal(g, cell[order])
+
+
+def test_fullsize_band_push_deposit(full):
+    import oracle
+    cfg, ps, sim = full
+    nt = cfg["nt"]
+    lo, hi = 1500, 1516            # particle start rows of the band (dipole PIC band, ~1.2e6 each)
+    base = {s: sim.particles(s) for s in range(2)}
+    ref = oracle.Oracle(dict(cfg, capacity=3_000_000, inject=False))
+    sel = {}
+    for s in range(2):
+        row = base[s]["cell"] // nt
+        sel[s] = np.flatnonzero((row >= lo) & (row <= hi))
+        ref.set_particles(s, {k: v[sel[s]] for k, v in base[s].items()})
+    assert len(sel[0]) > 10_000
+    sim.step_stages(1, ST["node"] | ST["push"])
+    ref.step(1, ST["node"] | ST["push"])
+    # J on rows whose every contribution comes from band particles
+    a, b = lo + 2, hi
+    for f in ("J_r", "J_th", "J_ph"):
+        gj, oj = sim.get(f)[a:b], ref.get(f)[a:b]
+        assert rel_l2(gj, oj) < 1e-5, (f, rel_l2(gj, oj))
+    for s in range(2):
+        g = {k: v[sel[s]] for k, v in sim.particles(s).items()}
+        o = ref.particles(s)
+        bad, ties, err = particle_mismatches(g, o, nt)
+        assert bad == 0, (s, bad, ties)
+        assert err < 1e-5
+        live = (g["cell"] >= 0) & (g["cell"] == o["cell"])
+        for k in ("ur", "ut", "up"):
+            assert rel_l2(g[k][live], o[k][live]) < 1e-5, k
+
+
+def test_fullsize_divb_after_steps(full):
+    cfg, ps, sim = full
+    sim.step(2)
+    nr, nt = cfg["nr"], cfg["nt"]
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / nr
+    rn = cfg["r_min"] * np.exp(np.arange(nr + 1) * d)
+    tn = np.arange(nt + 1) * math.pi / nt
+    br, bt = sim.get("B_r").astype(np.float64), sim.get("B_th").astype(np.float64)
+    ar = 2 * math.pi * rn[:, None] ** 2 * (np.cos(tn[:-1]) - np.cos(tn[1:]))[None, :]
+    at = math.pi * np.sin(tn)[None, :] * (rn[1:] ** 2 - rn[:-1] ** 2)[:, None]
+    flux = br[1:] * ar[1:] - br[:-1] * ar[:-1] + bt[:, 1:] * at[:, 1:] - bt[:, :-1] * at[:, :-1]
+    inside = rn[1:] < cfg["r_abs"]
+    scale = np.abs(br[:-1] * ar[:-1])[inside].max()
+    # FP32 fields: the discrete divergence is zero up to FP32 rounding of the fluxes
+    assert np.abs(flux[inside]).max() < 1e-5 * scale
+    assert sim.status() == 0
