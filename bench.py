@@ -117,6 +117,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_replicas(elapsed, counts, world_size):
+    """Replicas: wall time is the slowest rank's, work is the sum over ranks.
+    `elapsed` and `counts` are per-rank lists of floats; returns (max, sum)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(elapsed), dtype=torch.float64)
+    c = torch.tensor(list(counts), dtype=torch.float64)
+    if world_size > 1:
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else None
+        if dev is not None:
+            t, c = t.to(dev), c.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.cpu().tolist(), c.cpu().tolist()
+
+
 def oracle_rate(name, n_grid, steps, warm=0):
     """Particle-steps/s of the FP64 CPU oracle on a C3-shaped n x n sample."""
     import oracle
@@ -163,6 +179,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="c3")
+    ap.add_argument("--grid", type=int, default=0, help="run an n x n sample of the workload (same particles per cell)")
+    ap.add_argument("--pairs", type=int, default=0, help="override the number of e+- pairs")
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -187,12 +207,18 @@ def main():
         dist.barrier()
         __graft_entry__.build()
 
-    cfg = workloads.config(args.workload)
+    cfg = workloads.sample(args.workload, args.grid) if args.grid else workloads.config(args.workload)
+    if args.pairs:
+        cfg["n_pairs"] = args.pairs
+    if args.precision:
+        cfg["precision"] = args.precision
     cfg["seed"] = int(cfg["seed"]) + 1000 * rank
     cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
     prec = cfg.get("precision", "fp32")
     t0 = time.perf_counter()
     ps = workloads.particles(cfg, threads=16)
+    keep_fp64 = prec == "fp32" and ws == 1 and not args.no_fp64_compare
+    ps_keep = ps if keep_fp64 else None
     log(f"[bench] rank {rank}: generated {2 * cfg['n_pairs']} particles in {time.perf_counter() - t0:.1f} s")
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
@@ -248,14 +274,35 @@ def main():
         el_e2e = time.perf_counter() - te
         pst_e2e = (last.pushed_tiled + last.pushed_tail) - (ie.pushed_tiled + ie.pushed_tail)
         readback = last.readback_bytes
+        sim.close()
+        del sim, pinned
+        torch.cuda.empty_cache()
+        # the FP64 instantiation of the same kernels on the same workload
+        fp64 = None
+        if keep_fp64:
+            c64 = dict(cfg, precision="fp64")
+            sim64 = hff.Sim(c64, device=f"cuda:{local}", stream=stream)
+            for s_ in range(2):
+                sim64.load(s_, ps_keep[s_])
+            del ps_keep
+            sim64.step(3)
+            k64 = 5
+            a64 = sim64.info()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            sim64.step(k64)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            b64 = sim64.info()
+            el64 = e0.elapsed_time(e1) / 1e3
+            p64 = (b64.pushed_tiled + b64.pushed_tail) - (a64.pushed_tiled + a64.pushed_tail)
+            fp64 = {"value": p64 / el64, "unit": UNIT, "ms_per_step": 1e3 * el64 / k64, "steps": k64,
+                    "path": "same kernels instantiated in FP64 (fields, particles, deposit), same workload and launch configuration"}
+            sim64.close()
+            del sim64
 
-    tt = torch.tensor([el, el_e2e], dtype=torch.float64, device=dev)
-    cnt = torch.tensor([float(pst), float(pst_e2e)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-    el, el_e2e = float(tt[0]), float(tt[1])
-    pst_all, pst_e2e_all = float(cnt[0]), float(cnt[1])
+    (el, el_e2e), (pst_all, pst_e2e_all) = reduce_replicas([el, el_e2e], [float(pst), float(pst_e2e)], ws)
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -296,7 +343,7 @@ def main():
             "cells": cells,
             "sort_every": cfg["sort_every"],
             "tile": [cfg["tile_r"], cfg["tile_t"]],
-            "l2": "inputs larger than L2 (particle state %.1f GB)" % (n_live0 * bpp / 2 * 28 / 26 / 1e9),
+            "l2": "inputs larger than L2 (particle state %.1f GB)" % (n_live0 * (28 if prec == "fp32" else 52) / 1e9),
             "parallelism": "replicas" if ws > 1 else "single",
             "step_roofline_fraction": (bpp * pst_all / K + BYTES_PER_CELL_STEP[prec] * cells * ws) / (el / K) / 1e9 / (peak * ws),
             "device_status": status,
@@ -313,8 +360,10 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if fp64 is not None:
+        fp64["fp32_speedup"] = line["value"] / fp64["value"]
+        line["fp64_path"] = fp64
     print(json.dumps(line), flush=True)
-    sim.close()
     if ws > 1:
         dist.destroy_process_group()
 

@@ -14,6 +14,8 @@
 //    read and written once, fully coalesced.
 //  * k_push_tail -- particles appended since the last sort (injection) and
 //    the no-sort configuration: gathers through L1/L2 and global atomics.
+#include <type_traits>
+
 #include "hff_common.cuh"
 
 namespace hff {
@@ -142,6 +144,32 @@ __device__ __forceinline__ void gather(const M &m, int nr, int nt, int i, int j,
   b[2] = interp(m, [](const M &q, int a, int c) { return q.bp(a, c); }, kih, wih, kjh, wjh);
 }
 
+// Shared-memory versions of the gather and the deposit: every access is a
+// constant offset from one base offset per weight set, and the staged
+// region replicates the edge values of each array, which reproduces the
+// constant extrapolation of stag() without clamping.
+template <typename R>
+__device__ __forceinline__ R lerp4(const R *a, int o, int lt, R wi, R wj) {
+  const R a0 = a[o], a1 = a[o + 1], b0 = a[o + lt], b1 = a[o + lt + 1];
+  const R lo = a0 + wj * (a1 - a0), hi = b0 + wj * (b1 - b0);
+  return lo + wi * (hi - lo);
+}
+
+template <typename R>
+__device__ __forceinline__ void gather_sh(const SharedMesh<R> &m, int i, int j, R xo, R yo, R e[3], R b[3]) {
+  const bool hx = xo >= R(0.5), hy = yo >= R(0.5);
+  const int oc = m.o(i, j);
+  const int onn = oc, onh = oc - (hy ? 0 : 1), ohn = oc - (hx ? 0 : m.lt), ohh = ohn - (hy ? 0 : 1);
+  const R win = xo, wjn = yo, wih = hx ? xo - R(0.5) : xo + R(0.5), wjh = hy ? yo - R(0.5) : yo + R(0.5);
+  const int lt = m.lt;
+  e[0] = lerp4(m.s_er, ohn, lt, wih, wjn);
+  b[1] = lerp4(m.s_bt, ohn, lt, wih, wjn);
+  e[1] = lerp4(m.s_et, onh, lt, win, wjh);
+  b[0] = lerp4(m.s_br, onh, lt, win, wjh);
+  e[2] = lerp4(m.s_ep, onn, lt, win, wjn);
+  b[2] = lerp4(m.s_bp, ohh, lt, wih, wjh);
+}
+
 // Modified Boris step (Eqs. 15-17, c = 1): Lorentz Boris gives u_L, the
 // radiation-reaction kick K F_RR is evaluated at the time-centred momentum
 // (u + u_L)/2 and limited to half of |u_L| per step.  Bperp^2 of Eq. 17 is
@@ -179,11 +207,12 @@ __device__ __forceinline__ void boris_rr(R qm, R krr, R dt, const R u[3], const 
     const R du1 = k * ((f2 * b[0] - f0 * b[2]) + bdot * e[1] - g2 * bp2 * be1);
     const R du2 = k * ((f0 * b[1] - f1 * b[0]) + bdot * e[2] - g2 * bp2 * be2);
     const R dn2 = du0 * du0 + du1 * du1 + du2 * du2, ul2s = ul0 * ul0 + ul1 * ul1 + ul2 * ul2;
-    const R lim = (dn2 > R(0.25) * ul2s) ? R(0.5) * sqrt(ul2s * rcp(dn2)) : R(1);
+    const R lim = (dn2 > R(0.25) * ul2s) ? R(0.5) * rsq(dn2 * rcp(ul2s)) : R(1);
     out[0] = ul0 + lim * du0;
     out[1] = ul1 + lim * du1;
     out[2] = ul2 + lim * du2;
-    dgam = sqrt(R(1) + ul2s) - sqrt(R(1) + out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+    const R gl = R(1) + ul2s, go = R(1) + out[0] * out[0] + out[1] * out[1] + out[2] * out[2];
+    dgam = gl * rsq(gl) - go * rsq(go);
   }
 }
 
@@ -295,6 +324,42 @@ __device__ __forceinline__ Axis<R> axis_weights(R x0, R X1) {
   return w;
 }
 
+template <typename R>
+__device__ __forceinline__ void deposit_sh(const SharedMesh<R> &m, R qw, int i0, int j0, R x0, R y0, R X1, R Y1,
+                                           R vphi) {
+  const Axis<R> ax = axis_weights(x0, X1), ay = axis_weights(y0, Y1);
+  const R nq = -qw;
+  const int lt = m.lt;
+  const int ob = m.o(i0 - 1 + ax.a0, j0 - 1 + ay.a0);
+  {
+    const R g0 = nq * ax.f0, g1 = nq * ax.f1;
+    const R v[6] = {g0 * ay.m0, g0 * ay.m1, g0 * ay.m2, g1 * ay.m0, g1 * ay.m1, g1 * ay.m2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (v[k] != R(0)) atomicAdd(&m.s_jr[ob + (k / 3) * lt + k % 3], v[k]);
+  }
+  {
+    const R g0 = nq * ay.f0, g1 = nq * ay.f1;
+    const R v[6] = {g0 * ax.m0, g0 * ax.m1, g0 * ax.m2, g1 * ax.m0, g1 * ax.m1, g1 * ax.m2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (v[k] != R(0)) atomicAdd(&m.s_jt[ob + (k % 3) * lt + k / 3], v[k]);
+  }
+  {
+    const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
+    const int km = (xm < R(0)) ? -1 : (xm < R(1) ? 0 : 1);
+    const int lm = (ym < R(0)) ? -1 : (ym < R(1) ? 0 : 1);
+    const R wx = xm - R(km), wy = ym - R(lm);
+    const R qv = qw * vphi;
+    const R a0 = qv * (R(1) - wx), a1 = qv * wx;
+    const R v[4] = {a0 * (R(1) - wy), a0 * wy, a1 * (R(1) - wy), a1 * wy};
+    const int op = m.o(i0 + km, j0 + lm);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (v[k] != R(0)) atomicAdd(&m.s_jp[op + (k / 2) * lt + k % 2], v[k]);
+  }
+}
+
 template <typename R, typename M>
 __device__ __forceinline__ void deposit(const M &m, R qw, int i0, int j0, R x0, R y0, R X1, R Y1, R vphi) {
   const Axis<R> ax = axis_weights(x0, X1), ay = axis_weights(y0, Y1);
@@ -355,15 +420,17 @@ struct SpeciesConst {
 
 // One particle: gather, push, move, kill rules, deposit, store.
 template <typename R, typename M>
-__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const SpeciesConst<R> &K, int64_t q,
+__device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const SpeciesConst<R> &K, int q,
                                          int i, int j, Tally<R> &tl) {
+  constexpr bool kShared = std::is_same<M, SharedMesh<R>>::value;
   const Species<R> &S = K.S;
   const int nt = p.nt, nr = p.nr;
   const R xo = S.xo[q], yo = S.yo[q], w = S.w[q];
   R u[3] = {S.ur[q], S.ut[q], S.up[q]};
   R e[3], b[3], un[3], dg;
   tl.pushed += 1;
-  gather<R>(m, nr, nt, i, j, xo, yo, e, b);
+  if constexpr (kShared) gather_sh<R>(m, i, j, xo, yo, e, b);
+  else gather<R>(m, nr, nt, i, j, xo, yo, e, b);
   boris_rr<R>(K.qm, K.krr, p.dt, u, e, b, un, dg);
   tl.radiated += w * K.m * dg;
   // position of the particle: r = r_i exp(xo D), theta = theta_j + yo dtheta
@@ -411,7 +478,8 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
   int j1 = j + dj;
   if (j1 >= nt) { j1 = nt - 1; yn = one_minus_ulp<R>(); }
   if (!dead && m.ff(i1, j1)) dead = true;
-  deposit<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
+  if constexpr (kShared) deposit_sh<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
+  else deposit<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
   if (dead) {
     S.cell[q] = -1;
     tl.killed += w;
@@ -426,7 +494,7 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
 // out-of-region fallback of the tiled kernel (kept out of line so that the
 // hot loop stays small)
 template <typename R>
-__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int64_t q, int i, int j,
+__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int q, int i, int j,
                                              Tally<R> &tl) {
   GlobalMesh<R> g(p);
   push_one<R>(g, p, K, q, i, j, tl);
@@ -465,7 +533,7 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
       if (c < 0) continue;
       int i, j;
       decode_cell(p, c, i, j);
-      push_one<R>(m, p, K, q, i, j, tl);
+      push_one<R>(m, p, K, (int)q, i, j, tl);
     }
   }
   flush_tally(tl, p.acc, p.status, &p.pushed[1]);
@@ -499,18 +567,19 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl,
     const int ti = tile / p.ntt, tj = tile - ti * p.ntt;
     m.i0 = ti * p.tile_r - halo - 1;
     m.j0 = tj * p.tile_t - halo - 1;
-    // stage E, B, flags; clear J
+    // stage E, B, flags (edge values replicated outside each array); clear J
     for (int k = threadIdx.x; k < area; k += blockDim.x) {
       const int a = k / lt, c = k - a * lt;
       const int gi = m.i0 + a, gj = m.j0 + c;
-      const bool okr = gi >= 0, okj = gj >= 0;
-      m.s_er[k] = (okr && okj && gi < nr && gj <= nt) ? p.f.er[ix(gi, gj, n1)] : R(0);
-      m.s_et[k] = (okr && okj && gi <= nr && gj < nt) ? p.f.et[ix(gi, gj, nt)] : R(0);
-      m.s_ep[k] = (okr && okj && gi <= nr && gj <= nt) ? p.f.ep[ix(gi, gj, n1)] : R(0);
-      m.s_br[k] = (okr && okj && gi <= nr && gj < nt) ? p.f.br[ix(gi, gj, nt)] : R(0);
-      m.s_bt[k] = (okr && okj && gi < nr && gj <= nt) ? p.f.bt[ix(gi, gj, n1)] : R(0);
-      m.s_bp[k] = (okr && okj && gi < nr && gj < nt) ? p.f.bp[ix(gi, gj, nt)] : R(0);
-      m.s_ff[k] = (okr && okj && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
+      const int in = min(max(gi, 0), nr), ih = min(max(gi, 0), nr - 1);   // node / half rows
+      const int jn = min(max(gj, 0), nt), jh = min(max(gj, 0), nt - 1);   // node / half columns
+      m.s_er[k] = p.f.er[ix(ih, jn, n1)];
+      m.s_et[k] = p.f.et[ix(in, jh, nt)];
+      m.s_ep[k] = p.f.ep[ix(in, jn, n1)];
+      m.s_br[k] = p.f.br[ix(in, jh, nt)];
+      m.s_bt[k] = p.f.bt[ix(ih, jn, n1)];
+      m.s_bp[k] = p.f.bp[ix(ih, jh, nt)];
+      m.s_ff[k] = (gi >= 0 && gj >= 0 && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
       m.s_jr[k] = R(0); m.s_jt[k] = R(0); m.s_jp[k] = R(0);
     }
     for (int k = threadIdx.x; k < lr; k += blockDim.x) {
@@ -524,10 +593,10 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl,
     }
     const SpeciesConst<R> K(p, s);
     __syncthreads();
-    const int64_t q0 = item.z, q1 = (int64_t)item.z + item.w;
+    const int q0 = item.z, q1 = item.z + item.w;
     // a particle is handled in shared memory when its whole stencil (start
     // cell -1 .. +2 in both directions) lies inside the region
-    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
       const int c = p.sp[s].cell[q];
       if (c < 0) continue;
       int i, j;
