@@ -720,6 +720,11 @@ int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, voi
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm <= 0) nsm = 1;
   h->tail_grid = nsm * 4;
+  {
+    const size_t psm = (size_t)(cfg->nt + 1) * (cfg->precision == HFF_FP64 ? 8 : 4);
+    const cudaError_t e = cfg->precision == HFF_FP64 ? set_psi_smem<double>(psm) : set_psi_smem<float>(psm);
+    if (e != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the flux-prefix shared memory size"));
+  }
   if (cfg->precision == HFF_FP32) {
     fill_params<float>(h);
     rc = init_state<float>(h);

@@ -15,36 +15,49 @@ constexpr int kRowThreads = 128;
 
 // ------------------------------------------------------------ Psi (Eq. 27)
 // Psi(i, 0) = 0, Psi(i, j+1) = Psi(i, j) + B_r(i, j+1/2) r_i^2 dcp_j, an
-// inclusive prefix along theta accumulated in FP64.  One block per r row.
+// inclusive prefix along theta accumulated in FP64.  One block per r row:
+// the row is staged through shared memory (coalesced in and out), each
+// thread sums a contiguous chunk serially in FP64 (one conversion and one
+// add per element), one block-wide scan of the chunk totals gives the
+// offsets, and the prefix is rounded to the working precision.
+constexpr int kPsiThreads = 256;
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_psi(Params<R> p) {
-  const int i = blockIdx.x;
-  const int nt = p.nt;
+__global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
+  extern __shared__ __align__(16) unsigned char psmem[];
+  R *row = reinterpret_cast<R *>(psmem);  // nt + 1 values
+  __shared__ double warp_tot[kPsiThreads / 32];
+  const int i = blockIdx.x, nt = p.nt, tid = threadIdx.x;
   const R *br = p.f.br + (int64_t)i * nt;
-  R *psi = p.f.psi + (int64_t)i * (nt + 1);
-  const double r2 = p.t.r2n[i];
-  __shared__ double warp_tot[8];
-  __shared__ double carry;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { carry = 0.0; psi[0] = R(0); }
+  for (int j = tid; j < nt; j += kPsiThreads) row[j] = br[j] * (R)p.t.dcp[j];
   __syncthreads();
-  for (int seg = 0; seg < nt; seg += 256) {
-    const int j = seg + threadIdx.x;
-    double v = (j < nt) ? (double)br[j] * p.t.dcp[j] : 0.0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    double off = carry;
-    for (int w = 0; w < wid; ++w) off += warp_tot[w];
-    if (j < nt) psi[j + 1] = (R)(r2 * (off + v));
-    __syncthreads();
-    if (threadIdx.x == 255) carry = off + v;
-    __syncthreads();
+  const int chunk = (nt + kPsiThreads - 1) / kPsiThreads;
+  const int j0 = min(tid * chunk, nt), j1 = min(j0 + chunk, nt);
+  double acc = 0.0;
+  for (int j = j0; j < j1; ++j) acc += (double)row[j];
+  // exclusive scan of the chunk totals over the block
+  const int lane = tid & 31, wid = tid >> 5;
+  double x = acc;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  double off = x - acc;
+  for (int w = 0; w < wid; ++w) off += warp_tot[w];
+  const double r2 = p.t.r2n[i];
+  // rewrite the chunk in place with the prefix (inclusive, shifted by one)
+  double run = off;
+  R prev = (j0 < j1) ? row[j0] : R(0);
+  for (int j = j0; j < j1; ++j) {
+    run += (double)prev;
+    prev = (j + 1 < j1) ? row[j + 1] : R(0);
+    row[j] = (R)(r2 * run);  // becomes Psi(i, j+1)
+  }
+  __syncthreads();
+  R *psi = p.f.psi + (int64_t)i * (nt + 1);
+  for (int j = tid; j <= nt; j += kPsiThreads) psi[j] = (j == 0) ? R(0) : row[j - 1];
 }
 
 // ----------------------------------------------------------- collocation
@@ -280,7 +293,11 @@ __global__ void k_bc(Params<R> p) {
 static inline dim3 row_grid(int rows, int nt) { return dim3((nt + 1 + kRowThreads - 1) / kRowThreads, rows); }
 
 template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s) {
-  k_psi<R><<<p.nr + 1, 256, 0, s>>>(p);
+  const size_t smem = (size_t)(p.nt + 1) * sizeof(R);
+  k_psi<R><<<p.nr + 1, kPsiThreads, smem, s>>>(p);
+}
+template <typename R> cudaError_t set_psi_smem(size_t bytes) {
+  return cudaFuncSetAttribute(k_psi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s) {
   k_node_a<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
@@ -302,6 +319,7 @@ template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s) {
 
 #define HFF_INST(R)                                                            \
   template void launch_psi<R>(const Params<R> &, cudaStream_t);                \
+  template cudaError_t set_psi_smem<R>(size_t);                                \
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
