@@ -507,6 +507,7 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
 
 template <typename R>
 int enqueue_sort(hff_handle *h, int par, cudaStream_t s) {
+  if (h->c.capacity <= 0) return HFF_OK;  // nothing to sort
   Params<R> &p = params<R>(h)[par];
   Params<R> &q = params<R>(h)[par ^ 1];
   for (int sp = 0; sp < h->c.n_species; ++sp) {
