@@ -173,6 +173,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, hff, workloads, torch, ws, rank, local, dev):
+    """The 32-instance ensemble: every instance advanced by one graph launch
+    per step; value = particle-steps of all instances / wall time."""
+    import numpy as np
+    cfgs = workloads.ensemble(args.workload)
+    for c in cfgs:
+        c["seed"] = int(c["seed"]) + 1000 * rank
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        ens = hff.Ensemble(cfgs, device=f"cuda:{local}", stream=stream)
+        for k, c in enumerate(cfgs):
+            ps = workloads.particles(c, threads=16)
+            for s in range(2):
+                ens[k].load(s, ps[s])
+        torch.cuda.synchronize(dev)
+        n_live0 = sum(ens.info().count[:2])
+        K, W = args.steps, max(3, args.warmup)
+        ens.step(W)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        evb = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        eve = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ia = ens.info()
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize(dev)
+            ens.step_timed(evb, eve)
+            torch.cuda.synchronize(dev)
+        ib = ens.info()
+        el = evb[0].elapsed_time(eve[-1]) / 1e3
+        step_ms = [evb[k].elapsed_time(eve[k]) for k in range(K)]
+        pst = (ib.pushed_tiled + ib.pushed_tail) - (ia.pushed_tiled + ia.pushed_tail)
+        launches = ib.kernels_launched - ia.kernels_launched
+        status = ens.status()
+        ke = args.e2e_steps or K
+        ie = ens.info()
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter()
+        for k in range(ke):
+            ens.set_rr_scale(1.0)
+            ens.step(1)
+            last = ens.info()
+        el_e2e = time.perf_counter() - te
+        pst_e2e = (last.pushed_tiled + last.pushed_tail) - (ie.pushed_tiled + ie.pushed_tail)
+        readback = last.readback_bytes
+        ens.close()
+    (el, el_e2e), (pst_all, pst_e2e_all) = reduce_replicas([el, el_e2e], [float(pst), float(pst_e2e)], ws)
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    cells = sum(c["nr"] * c["nt"] for c in cfgs)
+    algo = BYTES_PER_PARTICLE_STEP["fp32"] * pst_all / K + BYTES_PER_CELL_STEP["fp32"] * cells * ws
+    achieved = algo / (statistics.mean(step_ms) / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": pst_all / el, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * el / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: ensemble of {len(cfgs)} independent instances "
+                               f"(grids 256-1024 x 128-512, R_LC 3-10, {n_live0} e+- at start), one graph launch per step",
+                   "cell_steps_per_s": ws * cells * K / el, "particles_per_step": pst_all / K, "cells": cells,
+                   "instances": len(cfgs), "sort_every": cfgs[0]["sort_every"],
+                   "l2": "per-step working set %.2f GB (of a 129 MB L2)" % (algo / 1e9),
+                   "parallelism": "replicas" if ws > 1 else "single", "device_status": status},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "whole ensemble step (one graph)", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": algo, "avg_launch_ms": statistics.mean(step_ms)},
+        "cpu_baseline": None,
+        "e2e": {"value": pst_e2e_all / el_e2e, "unit": UNIT, "h2d_bytes_per_step": 8,
+                "d2h_bytes_per_step": int(readback), "steps": ke,
+                "path": "hff_set_scalar + hff_step + hff_get_info per step (Python binding, pinned staging)"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +284,11 @@ def main():
         dist.barrier()
         __graft_entry__.build()
 
+    if args.workload == "c5":
+        run_ensemble(args, hff, workloads, torch, ws, rank, local, dev)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
     cfg = workloads.sample(args.workload, args.grid) if args.grid else workloads.config(args.workload)
     if args.pairs:
         cfg["n_pairs"] = args.pairs

@@ -136,6 +136,7 @@ typedef struct hff_info {
   int64_t pushed_tiled;     /* particle pushes by the tile-staged kernel (total) */
   int64_t pushed_tail;      /* particle pushes by the global-memory kernel       */
   int64_t readback_bytes;   /* bytes hff_get_info copies device -> host          */
+  int64_t n_inst;           /* instances behind the handle (ensemble: members)   */
 } hff_info;
 
 typedef struct hff_particle_view {
@@ -157,17 +158,31 @@ typedef struct hff_diag {
 
 typedef struct hff_handle hff_handle;
 
-/* Device bytes one instance of cfg needs (Sect. 4 grid, Sect. 3 particles).
- * n_inst must be 1.  Returns HFF_ERR_ARG for an invalid configuration. */
+/* Device bytes that n_inst instances need (Sect. 4 grid, Sect. 3 particles):
+ * cfg points to n_inst configurations (1 <= n_inst <= 4096); the total is the
+ * sum over the instances, each a multiple of 256 bytes.  The instances of an
+ * ensemble (n_inst > 1) must share precision and sort_every; grids, particle
+ * capacities, tiles, R_LC, seeds and every other field may differ.  Returns
+ * HFF_ERR_ARG for an invalid configuration (the message names the instance). */
 int hff_plan(const hff_config *cfg, int n_inst, size_t *bytes);
 
-/* Initialise an instance in caller-owned device memory dev_mem (>= the
+/* Initialise n_inst instances in caller-owned device memory dev_mem (>= the
  * planned bytes, 256-byte aligned) on the CUDA stream `stream` (cudaStream_t,
  * may be NULL for the legacy stream).  Builds the geometry in FP64 on the host,
  * the initial B from the analytic flux function of cfg->geom (Eqs. 32, 37) by
  * exact-area differences, E = 0 except the corotating star (Sect. 4), and no
  * particles.  *out receives a handle owned by the caller (free with
- * hff_destroy).  n_inst must be 1. */
+ * hff_destroy).
+ *
+ * Ensemble (n_inst > 1): the instances are independent simulations carved
+ * from dev_mem in order, addressed by `inst` in the per-instance calls
+ * below.  hff_step advances all of them in lockstep with ONE graph launch
+ * per step (and one per sort step): every instance's kernels form a parallel
+ * branch of that graph, so small instances fill the GPU together.
+ * hff_step_timed's events then bracket each whole ensemble step;
+ * hff_set_scalar applies to every instance; hff_get_info returns totals over
+ * the instances (n_inst = their number); hff_status reports the first
+ * instance with a latched error and clears all of them. */
 int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, void *stream,
              hff_handle **out);
 

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/hff.h: memory plan in caller-owned device
 // memory, FP64 host geometry and initial fields, the step as CUDA graphs
 // (one per particle-buffer parity, plus the sort), and the read-side calls.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -243,6 +244,13 @@ struct hff_handle {
   double *pin_scalar = nullptr;
   unsigned pin_next = 0;
   Small *pin_small = nullptr;
+  // ensemble (n_inst > 1): the members are ordinary instances carved from
+  // the caller's buffer; one graph holds every member's step as a parallel
+  // branch (fork streams joined by events at capture time)
+  std::vector<hff_handle *> members;
+  std::vector<cudaStream_t> fork;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t ev_fork = nullptr;
 };
 
 constexpr unsigned kScalarRing = 1024;
@@ -630,28 +638,192 @@ int do_stages(hff_handle *h, int32_t n, int32_t stages) {
   return HFF_OK;
 }
 
+// ------------------------------------------------------------ ensembles
+int max_inst() { return 4096; }
+
+int validate_all(const hff_config *cfg, int n_inst) {
+  if (!cfg) return fail(HFF_ERR_ARG, "null config");
+  if (n_inst < 1 || n_inst > max_inst()) return fail(HFF_ERR_ARG, "n_inst must be in [1, 4096]");
+  for (int k = 0; k < n_inst; ++k) {
+    const int rc = validate(&cfg[k]);
+    if (rc != HFF_OK) return n_inst > 1 ? fail(rc, "instance " + std::to_string(k) + ": " + g_err) : rc;
+    if (cfg[k].precision != cfg[0].precision || cfg[k].sort_every != cfg[0].sort_every)
+      return fail(HFF_ERR_ARG, "the instances of an ensemble share precision and sort_every");
+  }
+  return HFF_OK;
+}
+
+size_t planned_bytes(const hff_config &c) {
+  Offsets o;
+  layout(c, o);
+  return o.total;
+}
+
+bool is_ensemble(const hff_handle *h) { return !h->members.empty(); }
+
+// the instance `inst` of a handle (a plain instance is its own instance 0)
+hff_handle *member(hff_handle *h, int inst) {
+  if (!h) return nullptr;
+  if (!is_ensemble(h)) return inst == 0 ? h : nullptr;
+  return inst >= 0 && inst < (int)h->members.size() ? h->members[inst] : nullptr;
+}
+
+// Members loaded a different number of times sit on different buffer
+// parities; a sort of already-sorted particles only moves them to the other
+// buffer, so it brings every member to member 0's parity without changing a
+// result.
+template <typename R>
+int ens_align(hff_handle *e) {
+  const hff_handle *m0 = e->members[0];
+  for (hff_handle *m : e->members) {
+    if (m->step != m0->step) return fail(HFF_ERR_ARG, "the instances of an ensemble are at different steps");
+    if (m->parity != m0->parity) {
+      const int rc = run_sort_now<R>(m, m->st);
+      if (rc != HFF_OK) return rc;
+    }
+  }
+  return HFF_OK;
+}
+
+template <typename R>
+int ens_capture(hff_handle *e, bool sort, int par, cudaGraphExec_t *out, int64_t *nk) {
+  return capture(e, [&](cudaStream_t s) {
+    CK(cudaEventRecord(e->ev_fork, s));
+    for (size_t k = 0; k < e->members.size(); ++k) {
+      hff_handle *m = e->members[k];
+      CK(cudaStreamWaitEvent(e->fork[k], e->ev_fork, 0));
+      const int rc = sort ? enqueue_sort<R>(m, par, e->fork[k]) : enqueue_step<R>(m, par, HFF_ST_ALL, e->fork[k]);
+      if (rc != HFF_OK) return rc;
+      CK(cudaEventRecord(e->join[k], e->fork[k]));
+      CK(cudaStreamWaitEvent(s, e->join[k], 0));
+    }
+    return HFF_OK;
+  }, out, nk);
+}
+
+// One graph launch per ensemble step (plus one per sort step); evb / eve, if
+// given, bracket each whole step.
+template <typename R>
+int ens_step(hff_handle *e, int32_t n, void *const *evb, void *const *eve) {
+  int rc = ens_align<R>(e);
+  if (rc != HFF_OK) return rc;
+  const int every = e->c.sort_every;
+  for (int32_t k = 0; k < n; ++k) {
+    const int par = e->members[0]->parity;
+    if (!e->g_step[par]) {
+      rc = ens_capture<R>(e, false, par, &e->g_step[par], &e->k_step[par]);
+      if (rc != HFF_OK) return rc;
+    }
+    if (evb && evb[k]) CK(cudaEventRecord((cudaEvent_t)evb[k], e->st));
+    CK(cudaGraphLaunch(e->g_step[par], e->st));
+    e->launched += e->k_step[par];
+    for (hff_handle *m : e->members) m->step++;
+    e->step = e->members[0]->step;
+    if (every > 0 && e->step % every == 0) {
+      if (!e->g_sort[par]) {
+        rc = ens_capture<R>(e, true, par, &e->g_sort[par], &e->k_sort[par]);
+        if (rc != HFF_OK) return rc;
+      }
+      CK(cudaGraphLaunch(e->g_sort[par], e->st));
+      e->launched += e->k_sort[par];
+      for (hff_handle *m : e->members) m->parity ^= 1;
+      e->parity ^= 1;
+    }
+    if (eve && eve[k]) CK(cudaEventRecord((cudaEvent_t)eve[k], e->st));
+  }
+  return HFF_OK;
+}
+
+void destroy_handle(hff_handle *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (int p = 0; p < 2; ++p) {
+    if (h->g_step[p]) cudaGraphExecDestroy(h->g_step[p]);
+    if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
+    for (int k = 0; k < 3; ++k)
+      if (h->g_part[p][k]) cudaGraphExecDestroy(h->g_part[p][k]);
+  }
+  for (hff_handle *m : h->members) destroy_handle(m);
+  for (cudaStream_t f : h->fork) cudaStreamDestroy(f);
+  for (cudaEvent_t ev : h->join) cudaEventDestroy(ev);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
+  if (h->pin_scalar) cudaFreeHost(h->pin_scalar);
+  if (h->pin_small) cudaFreeHost(h->pin_small);
+  delete h;
+}
+
 }  // namespace
 
 // ==================================================================== ABI
 extern "C" {
 
 int hff_plan(const hff_config *cfg, int n_inst, size_t *bytes) {
-  if (n_inst != 1) return fail(HFF_ERR_ARG, "n_inst must be 1");
-  int rc = validate(cfg);
+  int rc = validate_all(cfg, n_inst);
   if (rc != HFF_OK) return rc;
   if (!bytes) return fail(HFF_ERR_ARG, "null bytes");
-  Offsets o;
-  layout(*cfg, o);
-  *bytes = o.total;
+  size_t total = 0;
+  for (int k = 0; k < n_inst; ++k) total += planned_bytes(cfg[k]);  // each a multiple of 256
+  *bytes = total;
   return HFF_OK;
 }
 
+static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *stream, hff_handle **out);
+
 int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, void *stream, hff_handle **out) {
-  if (n_inst != 1) return fail(HFF_ERR_ARG, "n_inst must be 1");
-  int rc = validate(cfg);
+  int rc = validate_all(cfg, n_inst);
   if (rc != HFF_OK) return rc;
   if (!dev_mem || !out) return fail(HFF_ERR_ARG, "null pointer");
   if (((uintptr_t)dev_mem & 255) != 0) return fail(HFF_ERR_ARG, "dev_mem must be 256-byte aligned");
+  if (n_inst == 1) return init_one(cfg, dev_mem, bytes, stream, out);
+  size_t need = 0;
+  for (int k = 0; k < n_inst; ++k) need += planned_bytes(cfg[k]);
+  if (bytes < need) return fail(HFF_ERR_CAPACITY, "dev_mem smaller than hff_plan bytes");
+  hff_handle *e = new hff_handle();
+  e->c = cfg[0];
+  e->st = (cudaStream_t)stream;
+  auto bail = [&](int code) {
+    const std::string msg = g_err;
+    destroy_handle(e);
+    g_err = msg;
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&e->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(HFF_ERR_CUDA, "stream or event create failed"));
+  double cap_sum = 0;
+  for (int k = 0; k < n_inst; ++k) cap_sum += (double)cfg[k].capacity;
+  size_t off = 0;
+  for (int k = 0; k < n_inst; ++k) {
+    hff_handle *m = nullptr;
+    const size_t b = planned_bytes(cfg[k]);
+    rc = init_one(&cfg[k], (char *)dev_mem + off, b, stream, &m);
+    if (rc != HFF_OK) return bail(fail(rc, "instance " + std::to_string(k) + ": " + g_err));
+    e->members.push_back(m);
+    off += b;
+    cudaStream_t f = nullptr;
+    cudaEvent_t j = nullptr;
+    if (cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "stream create failed"));
+    e->fork.push_back(f);
+    if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "event create failed"));
+    e->join.push_back(j);
+    // the members' persistent pushes run side by side: each gets a grid in
+    // proportion to its share of the particles, at least one block per SM
+    if (cap_sum > 0 && m->push_grid > 0) {
+      int dev = 0, nsm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int g = (int)std::ceil(m->push_grid * (double)cfg[k].capacity / cap_sum);
+      m->push_grid = std::min(m->push_grid, std::max(nsm, g));
+      m->tail_grid = std::min(m->tail_grid, std::max(nsm, (int)std::ceil(m->tail_grid * (double)cfg[k].capacity / cap_sum)));
+    }
+  }
+  *out = e;
+  return HFF_OK;
+}
+
+static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *stream, hff_handle **out) {
+  int rc;
   hff_handle *h = new hff_handle();
   h->c = *cfg;
   h->c.tile_r = tile_r_of(*cfg);
@@ -758,7 +930,8 @@ int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, voi
 
 int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const int32_t *cell, const void *xo,
                        const void *yo, const void *ur, const void *ut, const void *up, const void *w, int where) {
-  if (!h || inst != 0) return fail(HFF_ERR_ARG, "bad handle or instance");
+  h = member(h, inst);
+  if (!h) return fail(HFF_ERR_ARG, "bad handle or instance");
   if (species < 0 || species >= h->c.n_species) return fail(HFF_ERR_ARG, "bad species");
   if (n < 0) return fail(HFF_ERR_ARG, "negative count");
   if (n > h->c.capacity) return fail(HFF_ERR_CAPACITY, "more particles than capacity");
@@ -797,7 +970,8 @@ static int64_t field_elems(const hff_handle *h, int which) {
 }
 
 int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where) {
-  if (!h || inst != 0 || which < 0 || which > 5 || !src) return fail(HFF_ERR_ARG, "bad arguments");
+  h = member(h, inst);
+  if (!h || which < 0 || which > 5 || !src) return fail(HFF_ERR_ARG, "bad arguments");
   const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
   if (bytes != (size_t)field_elems(h, which) * R) return fail(HFF_ERR_ARG, "byte count does not match the field");
   CK(cudaMemcpyAsync(h->base + h->o.f[which], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
@@ -806,7 +980,8 @@ int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t by
 }
 
 int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int where) {
-  if (!h || inst != 0 || which < 0 || which > 15 || !dst) return fail(HFF_ERR_ARG, "bad arguments");
+  h = member(h, inst);
+  if (!h || which < 0 || which > 15 || !dst) return fail(HFF_ERR_ARG, "bad arguments");
   const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
   const size_t want = (size_t)field_elems(h, which) * (which == 9 ? 8 : R);
   if (bytes != want) return fail(HFF_ERR_ARG, "byte count does not match the field");
@@ -829,22 +1004,44 @@ int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int 
 
 int hff_step(hff_handle *h, int32_t nsteps) {
   if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h))
+    return h->c.precision == HFF_FP64 ? ens_step<double>(h, nsteps, nullptr, nullptr)
+                                      : ens_step<float>(h, nsteps, nullptr, nullptr);
   return h->c.precision == HFF_FP64 ? do_step<double>(h, nsteps) : do_step<float>(h, nsteps);
 }
 
 int hff_step_timed(hff_handle *h, int32_t nsteps, void *const *ev_begin, void *const *ev_end) {
   if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h))
+    return h->c.precision == HFF_FP64 ? ens_step<double>(h, nsteps, ev_begin, ev_end)
+                                      : ens_step<float>(h, nsteps, ev_begin, ev_end);
   return h->c.precision == HFF_FP64 ? do_step_timed<double>(h, nsteps, ev_begin, ev_end)
                                     : do_step_timed<float>(h, nsteps, ev_begin, ev_end);
 }
 
 int hff_step_stages(hff_handle *h, int32_t nsteps, int32_t stages) {
   if (!h || nsteps < 0) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h)) {
+    for (hff_handle *m : h->members) {
+      const int rc = hff_step_stages(m, nsteps, stages);
+      if (rc != HFF_OK) return rc;
+    }
+    h->step = h->members[0]->step;
+    return HFF_OK;
+  }
   return h->c.precision == HFF_FP64 ? do_stages<double>(h, nsteps, stages) : do_stages<float>(h, nsteps, stages);
 }
 
 int hff_set_scalar(hff_handle *h, int which, double value) {
   if (!h || which != HFF_SCALAR_RR_SCALE) return fail(HFF_ERR_ARG, "bad scalar");
+  if (is_ensemble(h)) {
+    for (hff_handle *m : h->members) {
+      const int rc = hff_set_scalar(m, which, value);
+      if (rc != HFF_OK) return rc;
+    }
+    h->c.rr_scale = value;
+    return HFF_OK;
+  }
   h->c.rr_scale = value;
   double *slot = h->pin_scalar + (h->pin_next++ % kScalarRing);
   *slot = value;
@@ -853,7 +1050,8 @@ int hff_set_scalar(hff_handle *h, int which, double value) {
 }
 
 int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out) {
-  if (!h || inst != 0 || species < 0 || species >= h->c.n_species || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  h = member(h, inst);
+  if (!h || species < 0 || species >= h->c.n_species || !out) return fail(HFF_ERR_ARG, "bad arguments");
   long long n = 0;
   CK(cudaMemcpyAsync(&n, &h->small->count[species], sizeof(n), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -866,7 +1064,8 @@ int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out) 
 }
 
 int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
-  if (!h || inst != 0 || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  h = member(h, inst);
+  if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
   const int nr = h->c.nr, nt = h->c.nt;
   double *q = reinterpret_cast<double *>(h->base + h->o.qnode);
   double *rows = reinterpret_cast<double *>(h->base + h->o.rows);
@@ -920,6 +1119,32 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
 
 int hff_get_info(hff_handle *h, hff_info *out) {
   if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h)) {  // totals over the members
+    hff_info sum;
+    std::memset(&sum, 0, sizeof(sum));
+    for (hff_handle *m : h->members) {
+      hff_info mi;
+      const int rc = hff_get_info(m, &mi);
+      if (rc != HFF_OK) return rc;
+      for (int s = 0; s < kMaxSpecies; ++s) sum.count[s] += mi.count[s];
+      sum.pushed_tiled += mi.pushed_tiled;
+      sum.pushed_tail += mi.pushed_tail;
+      sum.readback_bytes += mi.readback_bytes;
+      sum.n_inst += 1;
+    }
+    const hff_handle *m0 = h->members[0];
+    sum.dt = m0->dt;
+    sum.psi_unit = m0->psi_unit;
+    sum.step = m0->step;
+    sum.tile_r = m0->c.tile_r;
+    sum.tile_t = m0->c.tile_t;
+    sum.sort_every = h->c.sort_every;
+    sum.precision = h->c.precision;
+    sum.kernels_per_step = h->k_step[0] ? h->k_step[0] : h->k_step[1];
+    sum.kernels_launched = h->launched;
+    *out = sum;
+    return HFF_OK;
+  }
   CK(cudaMemcpyAsync(h->pin_small, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
   const Small &sm = *h->pin_small;
@@ -937,11 +1162,22 @@ int hff_get_info(hff_handle *h, hff_info *out) {
   out->pushed_tiled = (int64_t)sm.pushed[0];
   out->pushed_tail = (int64_t)sm.pushed[1];
   out->readback_bytes = (int64_t)sizeof(Small);
+  out->n_inst = 1;
   return HFF_OK;
 }
 
 int hff_status(hff_handle *h) {
   if (!h) return fail(HFF_ERR_ARG, "null handle");
+  if (is_ensemble(h)) {  // reads and clears every member; reports the first error
+    int first = HFF_OK;
+    std::string msg;
+    for (size_t k = 0; k < h->members.size(); ++k) {
+      const int rc = hff_status(h->members[k]);
+      if (rc != HFF_OK && first == HFF_OK) { first = rc; msg = "instance " + std::to_string(k) + ": " + g_err; }
+    }
+    if (first != HFF_OK) g_err = msg;
+    return first;
+  }
   unsigned st = 0, zero = 0;
   CK(cudaMemcpyAsync(&st, &h->small->status, sizeof(st), cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(&h->small->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
@@ -954,17 +1190,7 @@ int hff_status(hff_handle *h) {
 
 int hff_destroy(hff_handle *h) {
   if (!h) return fail(HFF_ERR_ARG, "null handle");
-  if (h->st) cudaStreamSynchronize(h->st);
-  for (int p = 0; p < 2; ++p) {
-    if (h->g_step[p]) cudaGraphExecDestroy(h->g_step[p]);
-    if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
-    for (int k = 0; k < 3; ++k)
-      if (h->g_part[p][k]) cudaGraphExecDestroy(h->g_part[p][k]);
-  }
-  if (h->cap_st) cudaStreamDestroy(h->cap_st);
-  if (h->pin_scalar) cudaFreeHost(h->pin_scalar);
-  if (h->pin_small) cudaFreeHost(h->pin_small);
-  delete h;
+  destroy_handle(h);
   return HFF_OK;
 }
 

@@ -296,9 +296,8 @@ template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s) {
   const size_t smem = (size_t)(p.nt + 1) * sizeof(R);
   k_psi<R><<<p.nr + 1, kPsiThreads, smem, s>>>(p);
 }
-template <typename R> cudaError_t set_psi_smem(size_t bytes) {
-  return cudaFuncSetAttribute(k_psi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+template <typename R> const void *psi_fn() { return reinterpret_cast<const void *>(&k_psi<R>); }
+template <typename R> cudaError_t set_psi_smem(size_t bytes) { return raise_smem_limit<psi_fn<R>>(bytes); }
 template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s) {
   k_node_a<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
 }

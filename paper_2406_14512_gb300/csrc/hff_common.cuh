@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace hff {
 
 constexpr int kMaxSpecies = 4;
@@ -14,6 +16,23 @@ constexpr int kMaxBreaks = 4;
 constexpr double kPi = 3.14159265358979323846;
 
 // status bits latched on the device
+// Raises (never lowers) the dynamic shared-memory limit of a kernel on the
+// current device.  The limit is a property of the kernel, shared by every
+// instance in the process, so instances with different tile sizes can live
+// side by side only if no instance ever lowers it under another.
+template <const void *(*Fn)()>
+inline cudaError_t raise_smem_limit(size_t bytes) {
+  static std::mutex mu;
+  static size_t cur[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && cur[dev] >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(Fn(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) cur[dev] = bytes;
+  return e;
+}
+
 constexpr unsigned kStCapacity = 1u;
 constexpr unsigned kStNonfinite = 2u;
 constexpr unsigned kStWorklist = 4u;

@@ -744,9 +744,8 @@ template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s) {
 template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s) {
   k_step_done<R><<<1, 32, 0, s>>>(p);
 }
-template <typename R> cudaError_t set_push_smem(size_t bytes) {
-  return cudaFuncSetAttribute(k_push_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+template <typename R> const void *push_tiled_fn() { return reinterpret_cast<const void *>(&k_push_tiled<R>); }
+template <typename R> cudaError_t set_push_smem(size_t bytes) { return raise_smem_limit<push_tiled_fn<R>>(bytes); }
 
 #define HFF_INST(R)                                                                         \
   template size_t push_tiled_smem<R>(const Params<R> &, int);                               \

@@ -55,7 +55,7 @@ class hff_info(C.Structure):
                 ("sort_every", C.c_int32), ("precision", C.c_int32),
                 ("kernels_per_step", C.c_int64), ("kernels_launched", C.c_int64),
                 ("pushed_tiled", C.c_int64), ("pushed_tail", C.c_int64),
-                ("readback_bytes", C.c_int64)]
+                ("readback_bytes", C.c_int64), ("n_inst", C.c_int64)]
 
 
 class hff_particle_view(C.Structure):
@@ -156,15 +156,27 @@ def config_struct(cfg: dict) -> hff_config:
 
 
 # ---------------------------------------------------------- C-named wrappers
-def hff_plan(cfg: hff_config, n_inst: int = 1) -> int:
+def _configs(cfg):
+    """One hff_config or a sequence of them -> (pointer, count)."""
+    if isinstance(cfg, hff_config):
+        return C.byref(cfg), 1
+    arr = (hff_config * len(cfg))(*cfg)
+    return arr, len(cfg)
+
+
+def hff_plan(cfg, n_inst: int | None = None) -> int:
+    """cfg: one hff_config, or a list of them for an ensemble."""
+    ptr, n = _configs(cfg)
     b = C.c_size_t()
-    _check(load().hff_plan(C.byref(cfg), n_inst, C.byref(b)))
+    _check(load().hff_plan(ptr, n if n_inst is None else n_inst, C.byref(b)))
     return b.value
 
 
-def hff_init(cfg: hff_config, dev_ptr: int, nbytes: int, stream: int, n_inst: int = 1):
+def hff_init(cfg, dev_ptr: int, nbytes: int, stream: int, n_inst: int | None = None):
+    ptr, n = _configs(cfg)
     h = C.c_void_p()
-    _check(load().hff_init(C.byref(cfg), n_inst, C.c_void_p(dev_ptr), nbytes, C.c_void_p(stream), C.byref(h)))
+    _check(load().hff_init(ptr, n if n_inst is None else n_inst, C.c_void_p(dev_ptr), nbytes,
+                           C.c_void_p(stream), C.byref(h)))
     return h
 
 
@@ -246,35 +258,14 @@ def hff_tile_order_noalloc(cell_ptr: int, n: int, nr: int, nt: int, tile_r: int,
 
 
 # ------------------------------------------------------------- convenience
-class Sim:
-    """One instance in a torch-owned device buffer on the current stream."""
+class _InstanceOps:
+    """Per-instance calls (fields, particles, diagnostics) of instance
+    ``self.inst`` behind handle ``self.h`` in buffer ``self.mem``."""
 
-    def __init__(self, cfg: dict, device: str = "cuda:0", stream=None):
-        import torch
-        if not torch.cuda.is_available():
-            raise HffError(HFF_ERR_CUDA, "no CUDA device: the hybrid step runs only on the GPU")
-        self.torch = torch
-        self.cfg = dict(cfg)
-        self.c = config_struct(cfg)
-        self.dev = torch.device(device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.dev)
-        self.nbytes = hff_plan(self.c)
-        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.dev)
-        self.h = hff_init(self.c, self.mem.data_ptr(), self.nbytes, self.stream.cuda_stream)
-        self.nr, self.nt = self.c.nr, self.c.nt
-        self.real = np.float64 if self.c.precision == FP64 else np.float32
-        self.tdtype = torch.float64 if self.c.precision == FP64 else torch.float32
-
-    def close(self):
-        if getattr(self, "h", None):
-            hff_destroy(self.h)
-            self.h = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+    def _setup(self, c: hff_config):
+        self.nr, self.nt = c.nr, c.nt
+        self.real = np.float64 if c.precision == FP64 else np.float32
+        self.tdtype = self.torch.float64 if c.precision == FP64 else self.torch.float32
 
     def shape(self, name: str):
         nr, nt = self.nr, self.nt
@@ -284,30 +275,30 @@ class Sim:
     def get(self, name: str) -> np.ndarray:
         dt = np.float64 if name == "psi" else self.real
         out = np.empty(self.shape(name), dt)
-        hff_fields(self.h, 0, FIELDS.index(name), out.ctypes.data, out.nbytes, HOST)
+        hff_fields(self.h, self.inst, FIELDS.index(name), out.ctypes.data, out.nbytes, HOST)
         return out
 
     def set(self, name: str, arr) -> None:
         a = np.ascontiguousarray(arr, dtype=self.real)
         assert a.shape == self.shape(name)
-        hff_set_field(self.h, 0, FIELDS.index(name), a.ctypes.data, a.nbytes, HOST)
+        hff_set_field(self.h, self.inst, FIELDS.index(name), a.ctypes.data, a.nbytes, HOST)
 
     def load(self, species: int, p: dict) -> None:
         n = len(p["cell"])
         arrs = [np.ascontiguousarray(p["cell"], np.int32)] + [
             np.ascontiguousarray(p[k], self.real) for k in ("xo", "yo", "ur", "ut", "up", "w")]
-        hff_load_particles(self.h, 0, species, n, [a.ctypes.data for a in arrs], HOST)
+        hff_load_particles(self.h, self.inst, species, n, [a.ctypes.data for a in arrs], HOST)
 
     def load_device(self, species: int, t: dict) -> None:
         n = int(t["cell"].numel())
-        hff_load_particles(self.h, 0, species, n,
+        hff_load_particles(self.h, self.inst, species, n,
                            [t[k].data_ptr() for k in ("cell", "xo", "yo", "ur", "ut", "up", "w")], DEVICE)
 
     def particle_views(self, species: int) -> dict:
         """Torch views (on the device, inside the instance buffer) of one
         species' particle arrays; valid until the next step."""
         torch = self.torch
-        v = hff_particles(self.h, 0, species)
+        v = hff_particles(self.h, self.inst, species)
         n, base = int(v.n), self.mem.data_ptr()
         out = {}
         for k, dt, sz in [("cell", torch.int32, 4)] + [(k, self.tdtype, np.dtype(self.real).itemsize)
@@ -320,13 +311,21 @@ class Sim:
         """Host copies of one species' particle arrays (slots in use)."""
         return {k: t.cpu().numpy() for k, t in self.particle_views(species).items()}
 
+    def diagnostics(self):
+        return hff_diagnostics(self.h, self.inst, self.nr)
+
+
+class _Stepping:
+    """Whole-handle calls (an instance or a whole ensemble)."""
+
     def step(self, n: int = 1) -> None:
         hff_step(self.h, n)
 
     def step_timed(self, ev_begin, ev_end) -> None:
         """One step per event pair (torch.cuda.Event with timing); the events
-        bracket the tiled push kernel.  Torch creates its CUDA events lazily,
-        so any event not yet created is recorded once here first."""
+        bracket the tiled push kernel of an instance, or the whole step of an
+        ensemble.  Torch creates its CUDA events lazily, so any event not yet
+        created is recorded once here first."""
         for e in list(ev_begin) + list(ev_end):
             if not e.cuda_event:
                 e.record(self.stream)
@@ -342,8 +341,71 @@ class Sim:
     def info(self) -> hff_info:
         return hff_get_info(self.h)
 
-    def diagnostics(self):
-        return hff_diagnostics(self.h, 0, self.nr)
-
     def status(self) -> int:
         return hff_status(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            hff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_and_stream(device, stream):
+    import torch
+    if not torch.cuda.is_available():
+        raise HffError(HFF_ERR_CUDA, "no CUDA device: the hybrid step runs only on the GPU")
+    dev = torch.device(device)
+    return torch, dev, (stream if stream is not None else torch.cuda.current_stream(dev))
+
+
+class Sim(_InstanceOps, _Stepping):
+    """One instance in a torch-owned device buffer on the current stream."""
+
+    def __init__(self, cfg: dict, device: str = "cuda:0", stream=None):
+        self.torch, self.dev, self.stream = _device_and_stream(device, stream)
+        self.cfg = dict(cfg)
+        self.c = config_struct(cfg)
+        self.inst = 0
+        self.nbytes = hff_plan(self.c)
+        self.mem = self.torch.empty(self.nbytes, dtype=self.torch.uint8, device=self.dev)
+        self.h = hff_init(self.c, self.mem.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        self._setup(self.c)
+
+
+class Member(_InstanceOps):
+    """Instance `inst` of an :class:`Ensemble` (fields, particles, diagnostics)."""
+
+    def __init__(self, ens: "Ensemble", inst: int):
+        self.ens, self.inst, self.torch, self.mem = ens, inst, ens.torch, ens.mem
+        self.cfg = ens.cfgs[inst]
+        self._setup(ens.cs[inst])
+
+    @property
+    def h(self):
+        return self.ens.h
+
+
+class Ensemble(_Stepping):
+    """Independent instances in one buffer, stepped together by one graph
+    launch per step; ``ens[k]`` gives instance k."""
+
+    def __init__(self, cfgs: list, device: str = "cuda:0", stream=None):
+        self.torch, self.dev, self.stream = _device_and_stream(device, stream)
+        self.cfgs = [dict(c) for c in cfgs]
+        self.cs = [config_struct(c) for c in cfgs]
+        self.nbytes = hff_plan(self.cs)
+        self.mem = self.torch.empty(self.nbytes, dtype=self.torch.uint8, device=self.dev)
+        self.h = hff_init(self.cs, self.mem.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        self.members = [Member(self, k) for k in range(len(cfgs))]
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, k: int) -> Member:
+        return self.members[k]

@@ -15,6 +15,9 @@ Workloads (shaped like the runs of Sects. 4-5; the paper uses no dataset):
       gamma ~ dN/dgamma ~ gamma^-2 on [1, 1e6], radiation reaction on,
       Goldreich-Julian top-up injection
   c4  8192 x 8192, r in [1, 200], R_LC = 20, 1e9 e+- (precision stress)
+  c5  an ensemble of 32 independent c2-like instances (seeds 1234..1265):
+      N_r in {256, 512, 1024}, N_theta in {128, 256, 512}, R_LC uniform in
+      [3, 10] with r_max = 10 R_LC, 1e5 - 5e6 e+- log-uniform (ensemble())
 Plus small variants of each for parity tests.
 
 Units: c = 1, r_star = 1, B_star = 1, e = 1 (species 0 = electrons q = -1,
@@ -110,6 +113,37 @@ def config(name: str) -> dict:
     else:
         raise KeyError(name)
     return c
+
+
+def ensemble(name: str = "c5", n_inst: int | None = None) -> list[dict]:
+    """Configurations of the independent instances of an ensemble workload.
+
+    c5: 32 c2-like instances (synthetic dipole / split monopole, Table 1 flux
+    bands, Maxwellian momenta, kappa-mode surface injection, FP32), instance k
+    drawn from seed 1234 + k.  small_c5: 4 instances of the same kind on grids
+    small enough for the oracle (parity tests)."""
+    if name == "c5":
+        n_inst = 32 if n_inst is None else n_inst
+        rows, cols, lo, hi = [256, 512, 1024], [128, 256, 512], 1e5, 5e6
+    elif name == "small_c5":
+        n_inst = 4 if n_inst is None else n_inst
+        rows, cols, lo, hi = [40, 56, 72], [32, 48, 64], 2e3, 8e3
+    else:
+        raise KeyError(name)
+    out = []
+    for k in range(n_inst):
+        seed = 1234 + k
+        rng = np.random.default_rng(seed)
+        nr, nt = int(rng.choice(rows)), int(rng.choice(cols))
+        r_lc = float(rng.uniform(3.0, 10.0))
+        n_part = float(np.exp(rng.uniform(math.log(lo), math.log(hi))))
+        c = _base(nr, nt, 10.0 * r_lc, r_lc, "synth", seed=seed)
+        n_pairs = max(1, int(round(n_part / 2)))
+        c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=n_pairs, steps=1000,
+                 precision="fp32", place="band", sheet_frac=0.2, momenta="maxwell",
+                 capacity=int(n_pairs * 1.2) + 20_000)
+        out.append(c)
+    return out
 
 
 def sample(name: str, n: int) -> dict:
