@@ -195,7 +195,11 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
                        const void *up, const void *w, int where);
 
 /* Overwrite field `which` (0..5) with `bytes` bytes from src (host or device).
- * The initial-B reference of the absorber is not changed. */
+ * B is held as the initial field B_0 plus a perturbation (the Yee update
+ * advances the perturbation, with curl B_0 precomputed in FP64), so setting
+ * B stores B - B_0 and reading it (hff_fields) returns the sum, each rounded
+ * once in the instance precision.  B_0 itself, also the absorber's reference,
+ * is not changed. */
 int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where);
 
 /* Copy field `which` (0..15, see the table above) into dst (host or device,

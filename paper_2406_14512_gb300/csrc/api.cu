@@ -132,7 +132,7 @@ struct Layout {
 };
 
 struct Offsets {
-  size_t f[19];          // er et ep br bt bp br0 bt0 bp0 jr jt jp psi jpr jpt jpp der det dep
+  size_t f[22];          // er et ep dbr dbt dbp br0 bt0 bp0 jr jt jp psi jpr jpt jpp der det dep sr st sp
   size_t ffcell;
   size_t tab_r[16];      // rn inv_rn rh inv_rh c_b2 c_bp2 c_e2 c_ep2 rho_a rho_b rh2 dep_r dep_t dep_p sig_n sig_h
   size_t tab_c[6];       // sn sh inv_sh inv_dcp inv_dch cn
@@ -170,10 +170,10 @@ void layout(const hff_config &c, Offsets &o) {
   Layout L;
   const size_t R = c.precision == HFF_FP64 ? 8 : 4;
   const size_t nr = c.nr, nt = c.nt, nn = (nr + 1) * (nt + 1);
-  const size_t sz[19] = {nr * (nt + 1), (nr + 1) * nt, nn, (nr + 1) * nt, nr * (nt + 1), nr * nt,
+  const size_t sz[22] = {nr * (nt + 1), (nr + 1) * nt, nn, (nr + 1) * nt, nr * (nt + 1), nr * nt,
                          (nr + 1) * nt, nr * (nt + 1), nr * nt, nr * (nt + 1), (nr + 1) * nt, nn,
-                         nn, nn, nn, nn, nn, nn, nn};
-  for (int k = 0; k < 19; ++k) o.f[k] = L.take(sz[k] * R);
+                         nn, nn, nn, nn, nn, nn, nn, nr * (nt + 1), (nr + 1) * nt, nn};
+  for (int k = 0; k < 22; ++k) o.f[k] = L.take(sz[k] * R);
   o.ffcell = L.take(nr * nt);
   const size_t rl[16] = {nr + 1, nr + 1, nr, nr, nr, nr, nr + 1, nr + 1, nr + 1, nr + 1, nr, nr, nr + 1, nr + 1, nr + 1, nr};
   for (int k = 0; k < 16; ++k) o.tab_r[k] = L.take(rl[k] * R);
@@ -310,9 +310,9 @@ void fill_params(hff_handle *h) {
     t.r2n = reinterpret_cast<const double *>(b + o.r2n);
     t.dcp = reinterpret_cast<const double *>(b + o.dcp);
     Fields<R> &f = p.f;
-    R **fp[19] = {&f.er, &f.et, &f.ep, &f.br, &f.bt, &f.bp, &f.br0, &f.bt0, &f.bp0, &f.jr, &f.jt, &f.jp,
-                  &f.psi, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep};
-    for (int k = 0; k < 19; ++k) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
+    R **fp[22] = {&f.er, &f.et, &f.ep, &f.br, &f.bt, &f.bp, &f.br0, &f.bt0, &f.bp0, &f.jr, &f.jt, &f.jp,
+                  &f.psi, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep, &f.sr, &f.st, &f.sp};
+    for (int k = 0; k < 22; ++k) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
     f.ffcell = reinterpret_cast<uint8_t *>(b + o.ffcell);
     const int pp = (c.sort_every > 0) ? par : 0;
     for (int s = 0; s < c.n_species; ++s) {
@@ -457,12 +457,38 @@ int init_state(hff_handle *h) {
     et[j] = -omega * g.rn(0) * std::sin(g.th(j)) * br[j];
     et[(size_t)nr * nt + j] = 0.0;
   }
+  // B is held as B_0 + dB: B_0 in the reference slots, dB = 0 (the buffer
+  // was cleared), and curl B_0 at the E locations in FP64 from the FP64 B_0,
+  // the same dual-face circulations as the Ampere kernel (Eq. 19)
   const std::vector<double> *F[6] = {&er, &et, &ep, &br, &bt, &bp};
-  for (int k = 0; k < 6; ++k)
+  for (int k = 0; k < 3; ++k)
     if ((rc = upload<R>(h, h->o.f[k], *F[k])) != HFF_OK) return rc;
-  if ((rc = upload<R>(h, h->o.f[6], br)) != HFF_OK) return rc;
-  if ((rc = upload<R>(h, h->o.f[7], bt)) != HFF_OK) return rc;
-  if ((rc = upload<R>(h, h->o.f[8], bp)) != HFF_OK) return rc;
+  for (int k = 3; k < 6; ++k)
+    if ((rc = upload<R>(h, h->o.f[k + 3], *F[k])) != HFF_OK) return rc;
+  {
+    std::vector<double> sr((size_t)nr * (nt + 1), 0.0), st((size_t)(nr + 1) * nt, 0.0),
+        sp((size_t)(nr + 1) * (nt + 1), 0.0);
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j <= nt; ++j) {
+        double v = 0.0;
+        if (j < nt) v += std::sin(g.th(j)) * bp[(size_t)i * nt + j];
+        if (j > 0) v -= std::sin(g.th(j - 1)) * bp[(size_t)i * nt + j - 1];
+        sr[(size_t)i * (nt + 1) + j] = v / (g.rh(i) * g.dch(j));
+      }
+    for (int i = 1; i < nr; ++i) {
+      const double lo = g.rlo(i), hi = g.rhi(i);
+      const double ce2 = 2.0 / (hi * hi - lo * lo), cep2 = 2.0 * (hi - lo) / ((hi * hi - lo * lo) * g.dth);
+      for (int j = 0; j < nt; ++j)
+        st[(size_t)i * nt + j] = -ce2 * (g.rh(i) * bp[(size_t)i * nt + j] - g.rh(i - 1) * bp[(size_t)(i - 1) * nt + j]);
+      for (int j = 1; j < nt; ++j)
+        sp[(size_t)i * (nt + 1) + j] =
+            ce2 * (g.rh(i) * bt[(size_t)i * (nt + 1) + j] - g.rh(i - 1) * bt[(size_t)(i - 1) * (nt + 1) + j]) -
+            cep2 * (br[(size_t)i * nt + j] - br[(size_t)i * nt + j - 1]);
+    }
+    if ((rc = upload<R>(h, h->o.f[19], sr)) != HFF_OK) return rc;
+    if ((rc = upload<R>(h, h->o.f[20], st)) != HFF_OK) return rc;
+    if ((rc = upload<R>(h, h->o.f[21], sp)) != HFF_OK) return rc;
+  }
   // injection targets: eligibility f < 1 at the frozen stellar surface
   // (Sect. 3) and kappa n_GJ V / w with n_GJ = Omega |B_r| / (2 pi e c)
   std::vector<int32_t> tgt(nt, 0);
@@ -957,6 +983,14 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
   return HFF_OK;
 }
 
+// dst = a + sign * (field at offset b_off), in the instance precision
+static void combine_field(hff_handle *h, void *dst, const void *a, size_t b_off, int64_t n, int sign) {
+  if (h->c.precision == HFF_FP64)
+    launch_combine<double>((double *)dst, (const double *)a, (const double *)(h->base + b_off), n, sign, h->st);
+  else
+    launch_combine<float>((float *)dst, (const float *)a, (const float *)(h->base + b_off), n, sign, h->st);
+}
+
 static int64_t field_elems(const hff_handle *h, int which) {
   const int64_t nr = h->c.nr, nt = h->c.nt;
   switch (which) {
@@ -974,7 +1008,17 @@ int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t by
   if (!h || which < 0 || which > 5 || !src) return fail(HFF_ERR_ARG, "bad arguments");
   const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
   if (bytes != (size_t)field_elems(h, which) * R) return fail(HFF_ERR_ARG, "byte count does not match the field");
-  CK(cudaMemcpyAsync(h->base + h->o.f[which], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  if (which < 3) {
+    CK(cudaMemcpyAsync(h->base + h->o.f[which], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  } else {  // B is held as B_0 + dB: store dB = B - B_0
+    const void *b = src;
+    if (where == HFF_HOST) {  // stage through the FP64 node scratch (>= any field)
+      CK(cudaMemcpyAsync(h->base + h->o.psi64, src, bytes, cudaMemcpyHostToDevice, h->st));
+      b = h->base + h->o.psi64;
+    }
+    combine_field(h, h->base + h->o.f[which], b, h->o.f[which + 3], field_elems(h, which), -1);
+    CK(cudaGetLastError());
+  }
   CK(cudaStreamSynchronize(h->st));
   return HFF_OK;
 }
@@ -996,7 +1040,14 @@ int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int 
     // offset table order: 0..5 fields, 6..8 initial B, 9..11 J, 12 psi,
     // 13..15 J_perp, 16..18 Delta E
     const int slot = which <= 5 ? which : which + 3;
-    CK(cudaMemcpyAsync(dst, h->base + h->o.f[slot], bytes, kind, h->st));
+    if (which >= 3 && which <= 5) {  // B = B_0 + dB
+      void *out = where == HFF_HOST ? (void *)(h->base + h->o.psi64) : dst;
+      combine_field(h, out, h->base + h->o.f[which + 3], h->o.f[which], field_elems(h, which), +1);
+      CK(cudaGetLastError());
+      if (where == HFF_HOST) CK(cudaMemcpyAsync(dst, out, bytes, kind, h->st));
+    } else {
+      CK(cudaMemcpyAsync(dst, h->base + h->o.f[slot], bytes, kind, h->st));
+    }
   }
   CK(cudaStreamSynchronize(h->st));
   return HFF_OK;

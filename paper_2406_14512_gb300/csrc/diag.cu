@@ -10,7 +10,7 @@ namespace hff {
 template <typename R>
 __global__ void __launch_bounds__(256) k_psi64(Params<R> p, double *out) {
   const int i = blockIdx.x, nt = p.nt;
-  const R *br = p.f.br + (int64_t)i * nt;
+  const R *br = p.f.br + (int64_t)i * nt, *br0 = p.f.br0 + (int64_t)i * nt;
   double *psi = out + (int64_t)i * (nt + 1);
   const double r2 = p.t.r2n[i];
   __shared__ double warp_tot[8];
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_psi64(Params<R> p, double *out) {
   __syncthreads();
   for (int seg = 0; seg < nt; seg += 256) {
     const int j = seg + threadIdx.x;
-    double v = (j < nt) ? (double)br[j] * p.t.dcp[j] : 0.0;
+    double v = (j < nt) ? ((double)br0[j] + (double)br[j]) * p.t.dcp[j] : 0.0;
     for (int o = 1; o < 32; o <<= 1) {
       const double y = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += y;
@@ -93,28 +93,32 @@ __global__ void __launch_bounds__(256) k_diag_rows(Params<R> p, DiagGeom g, cons
   __shared__ double sh[8];
   const int i = blockIdx.x, nr = p.nr, nt = p.nt, n1 = nt + 1;
   const Fields<R> &f = p.f;
+  // B = B_0 + dB, summed in FP64
+  auto Bt = [&](int64_t k) { return (double)f.bt0[k] + (double)f.bt[k]; };
+  auto Bp = [&](int64_t k) { return (double)f.bp0[k] + (double)f.bp[k]; };
+  auto Br = [&](int64_t k) { return (double)f.br0[k] + (double)f.br[k]; };
   double L = 0, ue = 0, ub = 0, gmax = 0, g2 = 0, gcnt = 0, rmax = 0;
   for (int j = threadIdx.x; j <= nt; j += blockDim.x) {
     if (i < nr) {
       const double r = g.rh[i];
       if (j < nt) {
         const double et = 0.5 * ((double)f.et[ix(i, j, nt)] + (double)f.et[ix(i + 1, j, nt)]);
-        L += et * (double)f.bp[ix(i, j, nt)] * 2 * kPi * r * r * g.dcp[j];
+        L += et * Bp(ix(i, j, nt)) * 2 * kPi * r * r * g.dcp[j];
       }
       const double epm = 0.5 * ((double)f.ep[ix(i, j, n1)] + (double)f.ep[ix(i + 1, j, n1)]);
-      L -= epm * (double)f.bt[ix(i, j, n1)] * 2 * kPi * r * r * g.dch[j];
+      L -= epm * Bt(ix(i, j, n1)) * 2 * kPi * r * r * g.dch[j];
       const double er = f.er[ix(i, j, n1)];
       ue += er * er * 2 * kPi * r * r * g.dch[j] * (g.rn[i + 1] - g.rn[i]);
-      const double bt = f.bt[ix(i, j, n1)];
+      const double bt = Bt(ix(i, j, n1));
       ub += bt * bt * kPi * g.sn[j] * (g.rn[i + 1] * g.rn[i + 1] - g.rn[i] * g.rn[i]) * r * (g.thi[j] - g.tlo[j]);
       if (j < nt) {
-        const double bp = f.bp[ix(i, j, nt)];
+        const double bp = Bp(ix(i, j, nt));
         ub += bp * bp * 0.5 * (g.rn[i + 1] * g.rn[i + 1] - g.rn[i] * g.rn[i]) * g.dth * 2 * kPi * r * g.sh[j];
       }
     }
     const double rlo = g.rlo[i], rhi = g.rhi[i], rni = g.rn[i];
     if (j < nt) {
-      const double et = f.et[ix(i, j, nt)], br = f.br[ix(i, j, nt)];
+      const double et = f.et[ix(i, j, nt)], br = Br(ix(i, j, nt));
       ue += et * et * kPi * g.sh[j] * (rhi * rhi - rlo * rlo) * rni * g.dth;
       ub += br * br * 2 * kPi * rni * rni * g.dcp[j] * (rhi - rlo);
     }

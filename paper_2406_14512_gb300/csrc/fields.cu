@@ -7,6 +7,12 @@
 // consecutive theta points of one r row (coalesced); blockIdx.y is the row.
 // All these kernels are HBM-bound stencils: each reads its inputs once per
 // step through L1/L2 (neighbour reuse hits cache) and writes its outputs once.
+//
+// B is held as the static initial field B_0 plus the perturbation dB, and
+// the Yee update advances dB only, with curl B_0 added as a source computed
+// once in FP64.  In FP32 the rounding of B then scales with |dB| instead of
+// |B|: near the star of a fine grid the rounding of a stored |B| ~ 1, divided
+// by a cell of 1e-3 r*, would otherwise enter E every step through the curl.
 #include "hff_common.cuh"
 
 namespace hff {
@@ -29,7 +35,8 @@ __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   __shared__ double warp_tot[kPsiThreads / 32];
   const int i = blockIdx.x, nt = p.nt, tid = threadIdx.x;
   const R *br = p.f.br + (int64_t)i * nt;
-  for (int j = tid; j < nt; j += kPsiThreads) row[j] = br[j] * (R)p.t.dcp[j];
+  const R *br0 = p.f.br0 + (int64_t)i * nt;
+  for (int j = tid; j < nt; j += kPsiThreads) row[j] = (br0[j] + br[j]) * (R)p.t.dcp[j];
   __syncthreads();
   const int chunk = (nt + kPsiThreads - 1) / kPsiThreads;
   const int j0 = min(tid * chunk, nt), j1 = min(j0 + chunk, nt);
@@ -71,13 +78,12 @@ __device__ __forceinline__ void collocate(const Params<R> &p, int i, int j, R e[
   e[0] = R(0.5) * (f.er[ix(i - 1, j, n1)] + f.er[ix(i, j, n1)]);
   e[1] = axis ? R(0) : R(0.5) * (f.et[ix(i, j - 1, nt)] + f.et[ix(i, j, nt)]);
   e[2] = axis ? R(0) : f.ep[ix(i, j, n1)];
-  b[0] = (j == 0) ? f.br[ix(i, 0, nt)]
-                  : (j == nt) ? f.br[ix(i, nt - 1, nt)]
-                              : R(0.5) * (f.br[ix(i, j - 1, nt)] + f.br[ix(i, j, nt)]);
-  b[1] = axis ? R(0) : R(0.5) * (f.bt[ix(i - 1, j, n1)] + f.bt[ix(i, j, n1)]);
-  b[2] = axis ? R(0)
-              : R(0.25) * (f.bp[ix(i - 1, j - 1, nt)] + f.bp[ix(i - 1, j, nt)] +
-                           f.bp[ix(i, j - 1, nt)] + f.bp[ix(i, j, nt)]);
+  auto br = [&](int a, int c) { const int64_t k = ix(a, c, nt); return f.br0[k] + f.br[k]; };
+  auto bt = [&](int a, int c) { const int64_t k = ix(a, c, n1); return f.bt0[k] + f.bt[k]; };
+  auto bp = [&](int a, int c) { const int64_t k = ix(a, c, nt); return f.bp0[k] + f.bp[k]; };
+  b[0] = (j == 0) ? br(i, 0) : (j == nt) ? br(i, nt - 1) : R(0.5) * (br(i, j - 1) + br(i, j));
+  b[1] = axis ? R(0) : R(0.5) * (bt(i - 1, j) + bt(i, j));
+  b[2] = axis ? R(0) : R(0.25) * (bp(i - 1, j - 1) + bp(i - 1, j) + bp(i, j - 1) + bp(i, j));
 }
 
 template <typename R> __device__ __forceinline__ R b2min();
@@ -122,8 +128,8 @@ __global__ void __launch_bounds__(kRowThreads) k_node_a(Params<R> p) {
 }
 
 // ---------------------------------------------------------------- Faraday
-// Eq. 18 over the exact primary faces, B -= h dt curl E; optionally the
-// absorber B -= sigma (B - B_0) afterwards.
+// Eq. 18 over the exact primary faces, dB -= h dt curl E; optionally the
+// absorber B -= sigma (B - B_0), i.e. dB -= sigma dB, afterwards.
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_faraday(Params<R> p, R hdt, bool absorb) {
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(kRowThreads) k_faraday(Params<R> p, R hdt, boo
     const R c = t.inv_rn[i] * (t.sn[j + 1] * f.ep[ix(i, j + 1, n1)] - t.sn[j] * f.ep[ix(i, j, n1)]) *
                 t.inv_dcp[j];
     R v = f.br[ix(i, j, nt)] - hdt * c;
-    if (absorb) { const R sg = t.sig_n[i]; if (sg > R(0)) v -= sg * (v - f.br0[ix(i, j, nt)]); }
+    if (absorb) { const R sg = t.sig_n[i]; if (sg > R(0)) v -= sg * v; }
     f.br[ix(i, j, nt)] = v;
   }
   if (i < nr) {
@@ -144,14 +150,14 @@ __global__ void __launch_bounds__(kRowThreads) k_faraday(Params<R> p, R hdt, boo
     if (j > 0 && j < nt) {
       v = f.bt[ix(i, j, n1)] +
           hdt * t.c_b2[i] * (t.rn[i + 1] * f.ep[ix(i + 1, j, n1)] - t.rn[i] * f.ep[ix(i, j, n1)]);
-      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) v -= sg * (v - f.bt0[ix(i, j, n1)]); }
+      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) v -= sg * v; }
     }
     f.bt[ix(i, j, n1)] = v;
     if (j < nt) {  // B_ph(i+1/2, j+1/2)
       const R c = t.c_b2[i] * (t.rn[i + 1] * f.et[ix(i + 1, j, nt)] - t.rn[i] * f.et[ix(i, j, nt)]) -
                   t.c_bp2[i] * (f.er[ix(i, j + 1, n1)] - f.er[ix(i, j, n1)]);
       R w = f.bp[ix(i, j, nt)] - hdt * c;
-      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) w -= sg * (w - f.bp0[ix(i, j, nt)]); }
+      if (absorb) { const R sg = t.sig_h[i]; if (sg > R(0)) w -= sg * w; }
       f.bp[ix(i, j, nt)] = w;
     }
   }
@@ -169,7 +175,8 @@ __device__ __forceinline__ R edge_r_mean(const R *a, int i, int j, int nr, int n
 }
 
 // ---------------------------------------------------------------- Ampere
-// Eq. 19 over the exact dual faces with J = (1 - f) J_PIC + f J_FFE (Eq. 28);
+// Eq. 19 over the exact dual faces, curl B = curl dB + curl B_0, with
+// J = (1 - f) J_PIC + f J_FFE (Eq. 28);
 // then the corotating star (tangential E fixed, Sect. 4), the conducting
 // outer wall, E_ph = 0 on the axis, the absorber on E, and J_PIC cleared.
 template <typename R>
@@ -188,21 +195,21 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
     const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
     const int64_t k = ix(i, j, n1);
     const R jt = (R(1) - fb) * f.jr[k] + fb * edge_r_mean(f.jpr, i, j, nr, n1);
-    f.er[k] = (f.er[k] + dt * c - fp * jt) * (R(1) - t.sig_h[i]);
+    f.er[k] = (f.er[k] + dt * (c + f.sr[k]) - fp * jt) * (R(1) - t.sig_h[i]);
     f.jr[k] = R(0);
   }
   if (j < nt) {  // E_th(i, j+1/2)
     const int64_t k = ix(i, j, nt);
     R v;
     if (i == 0) {
-      v = -p.omega * t.rn[0] * t.sh[j] * f.br[ix(0, j, nt)];
+      v = -p.omega * t.rn[0] * t.sh[j] * (f.br0[ix(0, j, nt)] + f.br[ix(0, j, nt)]);
     } else if (i == nr) {
       v = R(0);
     } else {
       const R c = -t.c_e2[i] * (t.rh[i] * f.bp[ix(i, j, nt)] - t.rh[i - 1] * f.bp[ix(i - 1, j, nt)]);
       const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
       const R jt = (R(1) - fb) * f.jt[k] + fb * R(0.5) * (f.jpt[ix(i, j, n1)] + f.jpt[ix(i, j + 1, n1)]);
-      v = (f.et[k] + dt * c - fp * jt) * (R(1) - t.sig_n[i]);
+      v = (f.et[k] + dt * (c + f.st[k]) - fp * jt) * (R(1) - t.sig_n[i]);
     }
     f.et[k] = v;
     f.jt[k] = R(0);
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
                   t.c_ep2[i] * (f.br[ix(i, j, nt)] - f.br[ix(i, j - 1, nt)]);
       const R fb = blend(p, f.psi[k]);
       const R jt = (R(1) - fb) * f.jp[k] + fb * f.jpp[k];
-      v = (f.ep[k] + dt * c - fp * jt) * (R(1) - t.sig_n[i]);
+      v = (f.ep[k] + dt * (c + f.sp[k]) - fp * jt) * (R(1) - t.sig_n[i]);
     }
     f.ep[k] = v;
     f.jp[k] = R(0);
@@ -280,7 +287,7 @@ __global__ void k_bc(Params<R> p) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j < nt) {
-    p.f.et[ix(0, j, nt)] = -p.omega * p.t.rn[0] * p.t.sh[j] * p.f.br[ix(0, j, nt)];
+    p.f.et[ix(0, j, nt)] = -p.omega * p.t.rn[0] * p.t.sh[j] * (p.f.br0[ix(0, j, nt)] + p.f.br[ix(0, j, nt)]);
     p.f.et[ix(nr, j, nt)] = R(0);
   }
   if (j <= nt) { p.f.ep[ix(0, j, n1)] = R(0); p.f.ep[ix(nr, j, n1)] = R(0); }
@@ -316,7 +323,19 @@ template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s) {
   k_bc<R><<<(n + 255) / 256, 256, 0, s>>>(p);
 }
 
+template <typename R>
+__global__ void k_combine(R *dst, const R *a, const R *b, int64_t n, R sign) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = a[k] + sign * b[k];
+}
+template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_t n, int sign, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t blocks = (n + 255) / 256;
+  k_combine<R><<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, s>>>(dst, a, b, n, (R)sign);
+}
+
 #define HFF_INST(R)                                                            \
+  template void launch_combine<R>(R *, const R *, const R *, int64_t, int, cudaStream_t); \
   template void launch_psi<R>(const Params<R> &, cudaStream_t);                \
   template cudaError_t set_psi_smem<R>(size_t);                                \
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \

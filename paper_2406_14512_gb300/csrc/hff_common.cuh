@@ -69,8 +69,10 @@ struct Tables {
 
 template <typename R>
 struct Fields {
-  R *er, *et, *ep, *br, *bt, *bp;   // E^n, B^n (B^{n+1/2} between the half steps)
-  R *br0, *bt0, *bp0;               // initial B (absorber reference)
+  R *er, *et, *ep;                  // E^n
+  R *br, *bt, *bp;                  // B^n - B_0 (B^{n+1/2} - B_0 between the half steps)
+  R *br0, *bt0, *bp0;               // initial field B_0 (also the absorber reference)
+  R *sr, *st, *sp;                  // curl B_0 at the E locations (computed in FP64)
   R *jr, *jt, *jp;                  // J_PIC accumulators (E locations)
   R *psi;                           // Psi at nodes (FP64 prefix, rounded to R)
   R *jpr, *jpt, *jpp;               // J_perp at nodes
@@ -155,6 +157,8 @@ template <typename R> void launch_faraday(const Params<R> &p, R half, bool absor
 template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s);
+// dst[k] = a[k] + sign * b[k], k < n (B <-> B - B_0 at the ABI)
+template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_t n, int sign, cudaStream_t s);
 
 struct WorkList {
   int4 *items;          // (species, tile, start, count)

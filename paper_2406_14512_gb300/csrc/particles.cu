@@ -29,9 +29,10 @@ struct GlobalMesh {
   __device__ __forceinline__ R er(int i, int j) const { return p.f.er[ix(i, j, p.nt + 1)]; }
   __device__ __forceinline__ R et(int i, int j) const { return p.f.et[ix(i, j, p.nt)]; }
   __device__ __forceinline__ R ep(int i, int j) const { return p.f.ep[ix(i, j, p.nt + 1)]; }
-  __device__ __forceinline__ R br(int i, int j) const { return p.f.br[ix(i, j, p.nt)]; }
-  __device__ __forceinline__ R bt(int i, int j) const { return p.f.bt[ix(i, j, p.nt + 1)]; }
-  __device__ __forceinline__ R bp(int i, int j) const { return p.f.bp[ix(i, j, p.nt)]; }
+  // B = B_0 + dB
+  __device__ __forceinline__ R br(int i, int j) const { const int64_t k = ix(i, j, p.nt); return p.f.br0[k] + p.f.br[k]; }
+  __device__ __forceinline__ R bt(int i, int j) const { const int64_t k = ix(i, j, p.nt + 1); return p.f.bt0[k] + p.f.bt[k]; }
+  __device__ __forceinline__ R bp(int i, int j) const { const int64_t k = ix(i, j, p.nt); return p.f.bp0[k] + p.f.bp[k]; }
   __device__ __forceinline__ bool ff(int i, int j) const { return p.f.ffcell[ix(i, j, p.nt)] != 0; }
   // raw charge flux through a dual face (J_r, J_th) or charge x velocity at
   // a node (J_ph), converted to a current density with the face area or
@@ -576,9 +577,10 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl,
       m.s_er[k] = p.f.er[ix(ih, jn, n1)];
       m.s_et[k] = p.f.et[ix(in, jh, nt)];
       m.s_ep[k] = p.f.ep[ix(in, jn, n1)];
-      m.s_br[k] = p.f.br[ix(in, jh, nt)];
-      m.s_bt[k] = p.f.bt[ix(ih, jn, n1)];
-      m.s_bp[k] = p.f.bp[ix(ih, jh, nt)];
+      const int64_t kb = ix(in, jh, nt), kt = ix(ih, jn, n1), kp = ix(ih, jh, nt);
+      m.s_br[k] = p.f.br0[kb] + p.f.br[kb];   // B = B_0 + dB
+      m.s_bt[k] = p.f.bt0[kt] + p.f.bt[kt];
+      m.s_bp[k] = p.f.bp0[kp] + p.f.bp[kp];
       m.s_ff[k] = (gi >= 0 && gj >= 0 && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
       m.s_jr[k] = R(0); m.s_jt[k] = R(0); m.s_jp[k] = R(0);
     }
