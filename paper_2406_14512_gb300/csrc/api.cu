@@ -142,6 +142,7 @@ struct Offsets {
   size_t small;          // counters block
   size_t surf, target, inj_prefix;
   size_t keys_a, keys_b, idx_a, idx_b, hist, spart, tstart, tend;
+  size_t sidx[kMaxSpecies];  // sorted order of the last sort, per species
   size_t items;
   size_t qnode, rows, psi64;
   int ntiles, ntt, max_items, nb, nparts;
@@ -186,6 +187,7 @@ void layout(const hff_config &c, Offsets &o) {
   const size_t cap = (size_t)c.capacity;
   const int parities = c.sort_every > 0 ? 2 : 1;
   std::memset(o.part, 0, sizeof(o.part));
+  std::memset(o.sidx, 0, sizeof(o.sidx));
   for (int p = 0; p < parities; ++p)
     for (int s = 0; s < c.n_species; ++s) {
       o.part[p][s][0] = L.take(cap * 4);
@@ -202,6 +204,7 @@ void layout(const hff_config &c, Offsets &o) {
   o.nparts = (int)(((size_t)o.nb * 256 + 4095) / 4096);
   o.max_items = c.n_species * (o.ntiles + (int)((cap + kChunk - 1) / kChunk)) + 1;
   if (c.sort_every > 0) {
+    for (int s = 0; s < c.n_species; ++s) o.sidx[s] = L.take(cap * 4);
     o.keys_a = L.take(cap * 4); o.keys_b = L.take(cap * 4);
     o.idx_a = L.take(cap * 4); o.idx_b = L.take(cap * 4);
     o.hist = L.take((size_t)o.nb * 256 * 4 + 4);
@@ -235,9 +238,12 @@ struct hff_handle {
   Small *small = nullptr;
   int parity = 0;
   int64_t step = 0;
-  cudaGraphExec_t g_step[2] = {nullptr, nullptr}, g_sort[2] = {nullptr, nullptr};
-  cudaGraphExec_t g_part[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-  int64_t k_step[2] = {0, 0}, k_sort[2] = {0, 0}, k_part[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  // a sort leaves the payload gather to the next push (pending): the step
+  // graphs are cached per [buffer parity][pending]
+  bool pending = false;
+  cudaGraphExec_t g_step[2][2] = {}, g_sort[2] = {nullptr, nullptr};
+  cudaGraphExec_t g_part[2][2][3] = {};
+  int64_t k_step[2][2] = {}, k_sort[2] = {0, 0}, k_part[2][2][3] = {};
   int64_t launched = 0;
   // pinned host staging: per-step scalars (a ring, so queued copies never
   // see a later value) and the counter readback
@@ -314,11 +320,15 @@ void fill_params(hff_handle *h) {
                   &f.psi, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep, &f.sr, &f.st, &f.sp};
     for (int k = 0; k < 22; ++k) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
     f.ffcell = reinterpret_cast<uint8_t *>(b + o.ffcell);
-    const int pp = (c.sort_every > 0) ? par : 0;
+    const int pp = (c.sort_every > 0) ? par : 0, po = (c.sort_every > 0) ? par ^ 1 : 0;
     for (int s = 0; s < c.n_species; ++s) {
       p.sp[s].cell = reinterpret_cast<int32_t *>(b + o.part[pp][s][0]);
       R **q[6] = {&p.sp[s].xo, &p.sp[s].yo, &p.sp[s].ur, &p.sp[s].ut, &p.sp[s].up, &p.sp[s].w};
       for (int k = 0; k < 6; ++k) *q[k] = reinterpret_cast<R *>(b + o.part[pp][s][k + 1]);
+      p.src[s].cell = reinterpret_cast<int32_t *>(b + o.part[po][s][0]);
+      R **r[6] = {&p.src[s].xo, &p.src[s].yo, &p.src[s].ur, &p.src[s].ut, &p.src[s].up, &p.src[s].w};
+      for (int k = 0; k < 6; ++k) *r[k] = reinterpret_cast<R *>(b + o.part[po][s][k + 1]);
+      p.sidx[s] = c.sort_every > 0 ? reinterpret_cast<const uint32_t *>(b + o.sidx[s]) : nullptr;
     }
     p.cap = c.capacity;
     p.count = h->small->count;
@@ -514,7 +524,7 @@ int init_state(hff_handle *h) {
 // --------------------------------------------------------- step enqueueing
 // parts: 1 = up to the tiled push, 2 = the tiled push, 4 = the rest
 template <typename R>
-int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts = 7) {
+int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts = 7, bool gather = false) {
   Params<R> &p = params<R>(h)[par];
   if ((parts & 1) && (stages & HFF_ST_NODE)) {
     launch_psi<R>(p, s);
@@ -523,7 +533,7 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
   if ((parts & 1) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
     CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
   if ((parts & 2) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
-    launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid);
+    launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid, gather);
   if (!(parts & 4)) {
     CK(cudaGetLastError());
     return HFF_OK;
@@ -540,12 +550,12 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
 }
 
 template <typename R>
-int enqueue_sort(hff_handle *h, int par, cudaStream_t s) {
+int enqueue_sort(hff_handle *h, int par, cudaStream_t s, bool gather) {
   if (h->c.capacity <= 0) return HFF_OK;  // nothing to sort
   Params<R> &p = params<R>(h)[par];
   Params<R> &q = params<R>(h)[par ^ 1];
   for (int sp = 0; sp < h->c.n_species; ++sp) {
-    launch_sort_species<R>(p, sp, q.sp[sp], h->ss, s);
+    launch_sort_species<R>(p, sp, q.sp[sp], h->ss, s, gather);
     launch_worklist<R>(p, &h->ss, h->wl, sp, sp == 0 ? 1 : 0, s);
   }
   CK(cudaGetLastError());
@@ -583,35 +593,63 @@ int capture(hff_handle *h, F &&fn, cudaGraphExec_t *out, int64_t *nk) {
   return HFF_OK;
 }
 
+// the deferred payload gather, done now (before anything reads particles)
+template <typename R>
+int materialize(hff_handle *h) {
+  if (!h->pending) return HFF_OK;
+  Params<R> &p = params<R>(h)[h->parity];
+  for (int sp = 0; sp < h->c.n_species; ++sp) launch_materialize<R>(p, sp, h->st);
+  CK(cudaGetLastError());
+  h->pending = false;
+  return HFF_OK;
+}
+int materialize_any(hff_handle *h) {
+  return h->c.precision == HFF_FP64 ? materialize<double>(h) : materialize<float>(h);
+}
+
+// a sort with its payload gather, now (loads and stage-by-stage stepping)
 template <typename R>
 int run_sort_now(hff_handle *h, cudaStream_t s) {
-  int rc = enqueue_sort<R>(h, h->parity, s);
+  int rc = materialize<R>(h);
+  if (rc != HFF_OK) return rc;
+  rc = enqueue_sort<R>(h, h->parity, s, true);
   if (rc != HFF_OK) return rc;
   h->parity ^= 1;
+  return HFF_OK;
+}
+
+// the sort at the end of a graph-replayed step: its payload moves with the
+// next push
+template <typename R>
+int graph_sort(hff_handle *h, int par) {
+  if (!h->g_sort[par]) {
+    const int rc = capture(h, [&](cudaStream_t s) { return enqueue_sort<R>(h, par, s, false); }, &h->g_sort[par],
+                           &h->k_sort[par]);
+    if (rc != HFF_OK) return rc;
+  }
+  CK(cudaGraphLaunch(h->g_sort[par], h->st));
+  h->launched += h->k_sort[par];
+  h->parity ^= 1;
+  h->pending = true;
   return HFF_OK;
 }
 
 template <typename R>
 int do_step(hff_handle *h, int32_t n) {
   for (int32_t k = 0; k < n; ++k) {
-    const int par = h->parity;
-    if (!h->g_step[par]) {
-      int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s); }, &h->g_step[par],
-                       &h->k_step[par]);
+    const int par = h->parity, gz = h->pending ? 1 : 0;
+    if (!h->g_step[par][gz]) {
+      int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s, 7, gz != 0); },
+                       &h->g_step[par][gz], &h->k_step[par][gz]);
       if (rc != HFF_OK) return rc;
     }
-    CK(cudaGraphLaunch(h->g_step[par], h->st));
-    h->launched += h->k_step[par];
+    CK(cudaGraphLaunch(h->g_step[par][gz], h->st));
+    h->launched += h->k_step[par][gz];
+    h->pending = false;
     h->step++;
     if (h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
-      if (!h->g_sort[par]) {
-        int rc = capture(h, [&](cudaStream_t s) { return enqueue_sort<R>(h, par, s); }, &h->g_sort[par],
-                         &h->k_sort[par]);
-        if (rc != HFF_OK) return rc;
-      }
-      CK(cudaGraphLaunch(h->g_sort[par], h->st));
-      h->launched += h->k_sort[par];
-      h->parity ^= 1;
+      const int rc = graph_sort<R>(h, par);
+      if (rc != HFF_OK) return rc;
     }
   }
   return HFF_OK;
@@ -620,31 +658,26 @@ int do_step(hff_handle *h, int32_t n) {
 template <typename R>
 int do_step_timed(hff_handle *h, int32_t n, void *const *evb, void *const *eve) {
   for (int32_t k = 0; k < n; ++k) {
-    const int par = h->parity;
+    const int par = h->parity, gz = h->pending ? 1 : 0;
     for (int part = 0; part < 3; ++part) {
-      if (!h->g_part[par][part]) {
+      if (!h->g_part[par][gz][part]) {
         const int mask = 1 << part;
-        int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s, mask); },
-                         &h->g_part[par][part], &h->k_part[par][part]);
+        int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s, mask, gz != 0); },
+                         &h->g_part[par][gz][part], &h->k_part[par][gz][part]);
         if (rc != HFF_OK) return rc;
       }
     }
-    CK(cudaGraphLaunch(h->g_part[par][0], h->st));
+    CK(cudaGraphLaunch(h->g_part[par][gz][0], h->st));
     if (evb && evb[k]) CK(cudaEventRecord((cudaEvent_t)evb[k], h->st));
-    CK(cudaGraphLaunch(h->g_part[par][1], h->st));
+    CK(cudaGraphLaunch(h->g_part[par][gz][1], h->st));
     if (eve && eve[k]) CK(cudaEventRecord((cudaEvent_t)eve[k], h->st));
-    CK(cudaGraphLaunch(h->g_part[par][2], h->st));
-    h->launched += h->k_part[par][0] + h->k_part[par][1] + h->k_part[par][2];
+    CK(cudaGraphLaunch(h->g_part[par][gz][2], h->st));
+    h->launched += h->k_part[par][gz][0] + h->k_part[par][gz][1] + h->k_part[par][gz][2];
+    h->pending = false;
     h->step++;
     if (h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
-      if (!h->g_sort[par]) {
-        int rc = capture(h, [&](cudaStream_t s) { return enqueue_sort<R>(h, par, s); }, &h->g_sort[par],
-                         &h->k_sort[par]);
-        if (rc != HFF_OK) return rc;
-      }
-      CK(cudaGraphLaunch(h->g_sort[par], h->st));
-      h->launched += h->k_sort[par];
-      h->parity ^= 1;
+      const int rc = graph_sort<R>(h, par);
+      if (rc != HFF_OK) return rc;
     }
   }
   return HFF_OK;
@@ -652,8 +685,10 @@ int do_step_timed(hff_handle *h, int32_t n, void *const *evb, void *const *eve) 
 
 template <typename R>
 int do_stages(hff_handle *h, int32_t n, int32_t stages) {
+  int rc = materialize<R>(h);
+  if (rc != HFF_OK) return rc;
   for (int32_t k = 0; k < n; ++k) {
-    int rc = enqueue_step<R>(h, h->parity, stages, h->st);
+    rc = enqueue_step<R>(h, h->parity, stages, h->st);
     if (rc != HFF_OK) return rc;
     h->step++;
     if ((stages & HFF_ST_SORT) && h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
@@ -697,28 +732,33 @@ hff_handle *member(hff_handle *h, int inst) {
 // Members loaded a different number of times sit on different buffer
 // parities; a sort of already-sorted particles only moves them to the other
 // buffer, so it brings every member to member 0's parity without changing a
-// result.
+// result.  Members whose deferred gather was done early by a read are
+// brought back in line by doing it for all.
 template <typename R>
 int ens_align(hff_handle *e) {
   const hff_handle *m0 = e->members[0];
+  bool mixed = false;
   for (hff_handle *m : e->members) {
     if (m->step != m0->step) return fail(HFF_ERR_ARG, "the instances of an ensemble are at different steps");
-    if (m->parity != m0->parity) {
-      const int rc = run_sort_now<R>(m, m->st);
-      if (rc != HFF_OK) return rc;
-    }
+    mixed = mixed || m->pending != m0->pending;
+  }
+  for (hff_handle *m : e->members) {
+    int rc = mixed ? materialize<R>(m) : HFF_OK;
+    if (rc == HFF_OK && m->parity != e->members[0]->parity) rc = run_sort_now<R>(m, m->st);
+    if (rc != HFF_OK) return rc;
   }
   return HFF_OK;
 }
 
 template <typename R>
-int ens_capture(hff_handle *e, bool sort, int par, cudaGraphExec_t *out, int64_t *nk) {
+int ens_capture(hff_handle *e, bool sort, int par, bool gather, cudaGraphExec_t *out, int64_t *nk) {
   return capture(e, [&](cudaStream_t s) {
     CK(cudaEventRecord(e->ev_fork, s));
     for (size_t k = 0; k < e->members.size(); ++k) {
       hff_handle *m = e->members[k];
       CK(cudaStreamWaitEvent(e->fork[k], e->ev_fork, 0));
-      const int rc = sort ? enqueue_sort<R>(m, par, e->fork[k]) : enqueue_step<R>(m, par, HFF_ST_ALL, e->fork[k]);
+      const int rc = sort ? enqueue_sort<R>(m, par, e->fork[k], false)
+                          : enqueue_step<R>(m, par, HFF_ST_ALL, e->fork[k], 7, gather);
       if (rc != HFF_OK) return rc;
       CK(cudaEventRecord(e->join[k], e->fork[k]));
       CK(cudaStreamWaitEvent(s, e->join[k], 0));
@@ -735,24 +775,24 @@ int ens_step(hff_handle *e, int32_t n, void *const *evb, void *const *eve) {
   if (rc != HFF_OK) return rc;
   const int every = e->c.sort_every;
   for (int32_t k = 0; k < n; ++k) {
-    const int par = e->members[0]->parity;
-    if (!e->g_step[par]) {
-      rc = ens_capture<R>(e, false, par, &e->g_step[par], &e->k_step[par]);
+    const int par = e->members[0]->parity, gz = e->members[0]->pending ? 1 : 0;
+    if (!e->g_step[par][gz]) {
+      rc = ens_capture<R>(e, false, par, gz != 0, &e->g_step[par][gz], &e->k_step[par][gz]);
       if (rc != HFF_OK) return rc;
     }
     if (evb && evb[k]) CK(cudaEventRecord((cudaEvent_t)evb[k], e->st));
-    CK(cudaGraphLaunch(e->g_step[par], e->st));
-    e->launched += e->k_step[par];
-    for (hff_handle *m : e->members) m->step++;
+    CK(cudaGraphLaunch(e->g_step[par][gz], e->st));
+    e->launched += e->k_step[par][gz];
+    for (hff_handle *m : e->members) { m->step++; m->pending = false; }
     e->step = e->members[0]->step;
     if (every > 0 && e->step % every == 0) {
       if (!e->g_sort[par]) {
-        rc = ens_capture<R>(e, true, par, &e->g_sort[par], &e->k_sort[par]);
+        rc = ens_capture<R>(e, true, par, false, &e->g_sort[par], &e->k_sort[par]);
         if (rc != HFF_OK) return rc;
       }
       CK(cudaGraphLaunch(e->g_sort[par], e->st));
       e->launched += e->k_sort[par];
-      for (hff_handle *m : e->members) m->parity ^= 1;
+      for (hff_handle *m : e->members) { m->parity ^= 1; m->pending = true; }
       e->parity ^= 1;
     }
     if (eve && eve[k]) CK(cudaEventRecord((cudaEvent_t)eve[k], e->st));
@@ -764,10 +804,12 @@ void destroy_handle(hff_handle *h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   for (int p = 0; p < 2; ++p) {
-    if (h->g_step[p]) cudaGraphExecDestroy(h->g_step[p]);
     if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
-    for (int k = 0; k < 3; ++k)
-      if (h->g_part[p][k]) cudaGraphExecDestroy(h->g_part[p][k]);
+    for (int g = 0; g < 2; ++g) {
+      if (h->g_step[p][g]) cudaGraphExecDestroy(h->g_step[p][g]);
+      for (int k = 0; k < 3; ++k)
+        if (h->g_part[p][g][k]) cudaGraphExecDestroy(h->g_part[p][g][k]);
+    }
   }
   for (hff_handle *m : h->members) destroy_handle(m);
   for (cudaStream_t f : h->fork) cudaStreamDestroy(f);
@@ -960,6 +1002,10 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
   if (!h) return fail(HFF_ERR_ARG, "bad handle or instance");
   if (species < 0 || species >= h->c.n_species) return fail(HFF_ERR_ARG, "bad species");
   if (n < 0) return fail(HFF_ERR_ARG, "negative count");
+  {
+    const int rc = materialize_any(h);  // the other species keep their particles
+    if (rc != HFF_OK) return rc;
+  }
   if (n > h->c.capacity) return fail(HFF_ERR_CAPACITY, "more particles than capacity");
   const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
   const int pp = (h->c.sort_every > 0) ? h->parity : 0;
@@ -1103,6 +1149,10 @@ int hff_set_scalar(hff_handle *h, int which, double value) {
 int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out) {
   h = member(h, inst);
   if (!h || species < 0 || species >= h->c.n_species || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  {
+    const int rc = materialize_any(h);
+    if (rc != HFF_OK) return rc;
+  }
   long long n = 0;
   CK(cudaMemcpyAsync(&n, &h->small->count[species], sizeof(n), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -1117,6 +1167,10 @@ int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out) 
 int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
   h = member(h, inst);
   if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  {
+    const int rc = materialize_any(h);
+    if (rc != HFF_OK) return rc;
+  }
   const int nr = h->c.nr, nt = h->c.nt;
   double *q = reinterpret_cast<double *>(h->base + h->o.qnode);
   double *rows = reinterpret_cast<double *>(h->base + h->o.rows);
@@ -1191,7 +1245,7 @@ int hff_get_info(hff_handle *h, hff_info *out) {
     sum.tile_t = m0->c.tile_t;
     sum.sort_every = h->c.sort_every;
     sum.precision = h->c.precision;
-    sum.kernels_per_step = h->k_step[0] ? h->k_step[0] : h->k_step[1];
+    sum.kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
     sum.kernels_launched = h->launched;
     *out = sum;
     return HFF_OK;
@@ -1208,7 +1262,7 @@ int hff_get_info(hff_handle *h, hff_info *out) {
   out->tile_t = h->c.tile_t;
   out->sort_every = h->c.sort_every;
   out->precision = h->c.precision;
-  out->kernels_per_step = h->k_step[0] ? h->k_step[0] : h->k_step[1];
+  out->kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
   out->kernels_launched = h->launched;
   out->pushed_tiled = (int64_t)sm.pushed[0];
   out->pushed_tail = (int64_t)sm.pushed[1];

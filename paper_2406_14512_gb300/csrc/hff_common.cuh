@@ -101,6 +101,11 @@ struct Params {
   Tables<R> t;
   Fields<R> f;
   Species<R> sp[kMaxSpecies];
+  // the other buffer parity and the sorted order of the last sort: the first
+  // push after a sort reads particle sidx[s][q] of src[s] and writes slot q
+  // of sp[s] (the sort's payload gather, done by the push)
+  Species<R> src[kMaxSpecies];
+  const uint32_t *sidx[kMaxSpecies];
   int64_t cap;
   long long *count;         // [kMaxSpecies] slots in use (device)
   long long *count_sorted;  // [kMaxSpecies] length of the tile-sorted prefix
@@ -170,7 +175,7 @@ struct WorkList {
 
 template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, int grid);
 template <typename R> void launch_push_tiled(const Params<R> &p, const WorkList &wl, int halo,
-                                             cudaStream_t s, int grid);
+                                             cudaStream_t s, int grid, bool gather);
 template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo);
 template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s);
@@ -187,8 +192,14 @@ struct SortScratch {
   int ntiles;
 };
 
+// Sort one species of parity p into the other parity dst.  The sorted order
+// is left in p.sidx[species]; with gather the payload moves now, otherwise
+// only the count and the removed slots of dst are set and the next push moves
+// the payload (launch_materialize does it eagerly).
 template <typename R> void launch_sort_species(const Params<R> &p, int species, Species<R> dst,
-                                               const SortScratch &ss, cudaStream_t s);
+                                               const SortScratch &ss, cudaStream_t s, bool gather);
+// the deferred payload gather of a species, src -> sp by sidx (slots < count)
+template <typename R> void launch_materialize(const Params<R> &p, int species, cudaStream_t s);
 template <typename R> void launch_worklist(const Params<R> &p, const SortScratch *ss,
                                            const WorkList &wl, int species, int first,
                                            cudaStream_t s);

@@ -410,24 +410,31 @@ struct Tally {
   unsigned pushed;
 };
 
-// per-species constants of a push, loaded once per work item
+// per-species constants of a push, loaded once per work item.  In (read)
+// and S (written) are the same arrays, except in the first push after a sort,
+// which reads the unsorted parity through the sorted order sidx.
 template <typename R>
 struct SpeciesConst {
-  Species<R> S;
+  Species<R> S, In;
+  const uint32_t *sidx;
   R qm, krr, q, m;
-  __device__ __forceinline__ SpeciesConst(const Params<R> &p, int s)
-      : S(p.sp[s]), qm(p.qm[s]), krr(p.krr[s] * (R)(*p.rr_scale)), q(p.q[s]), m(p.m[s]) {}
+  __device__ __forceinline__ SpeciesConst(const Params<R> &p, int s, bool gather = false)
+      : S(p.sp[s]), In(gather ? p.src[s] : p.sp[s]), sidx(p.sidx[s]), qm(p.qm[s]),
+        krr(p.krr[s] * (R)(*p.rr_scale)), q(p.q[s]), m(p.m[s]) {}
 };
 
-// One particle: gather, push, move, kill rules, deposit, store.
-template <typename R, typename M>
+// One particle: gather, push, move, kill rules, deposit, store.  Reads
+// particle qi of K.In and writes slot q of K.S (the same particle unless the
+// push also performs a sort's payload gather, kGather, which writes w too).
+template <typename R, bool kGather, typename M>
 __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const SpeciesConst<R> &K, int q,
-                                         int i, int j, Tally<R> &tl) {
+                                         int qi, int i, int j, Tally<R> &tl) {
   constexpr bool kShared = std::is_same<M, SharedMesh<R>>::value;
   const Species<R> &S = K.S;
+  const Species<R> &In = K.In;
   const int nt = p.nt, nr = p.nr;
-  const R xo = S.xo[q], yo = S.yo[q], w = S.w[q];
-  R u[3] = {S.ur[q], S.ut[q], S.up[q]};
+  const R xo = In.xo[qi], yo = In.yo[qi], w = In.w[qi];
+  R u[3] = {In.ur[qi], In.ut[qi], In.up[qi]};
   R e[3], b[3], un[3], dg;
   tl.pushed += 1;
   if constexpr (kShared) gather_sh<R>(m, i, j, xo, yo, e, b);
@@ -489,16 +496,17 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
   S.cell[q] = i1 * nt + j1;
   S.xo[q] = xn; S.yo[q] = yn;
   S.ur[q] = uo[0]; S.ut[q] = uo[1]; S.up[q] = uo[2];
+  if constexpr (kGather) S.w[q] = w;
   if (i1 == 0 && p.inject) atomicAdd(&p.surf[j1], 1);
 }
 
 // out-of-region fallback of the tiled kernel (kept out of line so that the
 // hot loop stays small)
-template <typename R>
-__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int q, int i, int j,
-                                             Tally<R> &tl) {
+template <typename R, bool kGather>
+__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int q, int qi, int i,
+                                             int j, Tally<R> &tl) {
   GlobalMesh<R> g(p);
-  push_one<R>(g, p, K, q, i, j, tl);
+  push_one<R, kGather>(g, p, K, q, qi, i, j, tl);
 }
 
 template <typename R>
@@ -534,7 +542,7 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
       if (c < 0) continue;
       int i, j;
       decode_cell(p, c, i, j);
-      push_one<R>(m, p, K, (int)q, i, j, tl);
+      push_one<R, false>(m, p, K, (int)q, (int)q, i, j, tl);
     }
   }
   flush_tally(tl, p.acc, p.status, &p.pushed[1]);
@@ -543,7 +551,7 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
 // ---------------------------------------------------------- tiled kernel
 // Region of a tile: cells [ti*TR - H, (ti+1)*TR + H) (and likewise in theta)
 // widened by the stencil: one node below, two above.
-template <typename R>
+template <typename R, bool kGather>
 __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl, int halo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
@@ -593,20 +601,24 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl,
       m.s_sn[k] = (gj >= 0 && gj <= nt) ? p.t.sn[gj] : R(0);
       m.s_cn[k] = (gj >= 0 && gj <= nt) ? p.t.cn[gj] : R(1);
     }
-    const SpeciesConst<R> K(p, s);
+    const SpeciesConst<R> K(p, s, kGather);
     __syncthreads();
     const int q0 = item.z, q1 = item.z + item.w;
     // a particle is handled in shared memory when its whole stencil (start
     // cell -1 .. +2 in both directions) lies inside the region
     for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      const int c = p.sp[s].cell[q];
-      if (c < 0) continue;
+      const int qi = kGather ? (int)K.sidx[q] : q;
+      const int c = K.In.cell[qi];
+      if (c < 0) {
+        if (kGather) K.S.cell[q] = -1;
+        continue;
+      }
       int i, j;
       decode_cell(p, c, i, j);
       if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-        push_one<R>(m, p, K, q, i, j, tl);
+        push_one<R, kGather>(m, p, K, q, qi, i, j, tl);
       else
-        push_one_global<R>(p, K, q, i, j, tl);
+        push_one_global<R, kGather>(p, K, q, qi, i, j, tl);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < area; k += blockDim.x) {
@@ -635,8 +647,9 @@ template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, 
   k_push_tail<R><<<grid, 256, 0, s>>>(p);
 }
 template <typename R> void launch_push_tiled(const Params<R> &p, const WorkList &wl, int halo,
-                                             cudaStream_t s, int grid) {
-  k_push_tiled<R><<<grid, 256, push_tiled_smem(p, halo), s>>>(p, wl, halo);
+                                             cudaStream_t s, int grid, bool gather) {
+  if (gather) k_push_tiled<R, true><<<grid, 256, push_tiled_smem(p, halo), s>>>(p, wl, halo);
+  else k_push_tiled<R, false><<<grid, 256, push_tiled_smem(p, halo), s>>>(p, wl, halo);
 }
 
 // ------------------------------------------------------------- injection
@@ -746,13 +759,16 @@ template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s) {
 template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s) {
   k_step_done<R><<<1, 32, 0, s>>>(p);
 }
-template <typename R> const void *push_tiled_fn() { return reinterpret_cast<const void *>(&k_push_tiled<R>); }
-template <typename R> cudaError_t set_push_smem(size_t bytes) { return raise_smem_limit<push_tiled_fn<R>>(bytes); }
+template <typename R, bool G> const void *push_tiled_fn() { return reinterpret_cast<const void *>(&k_push_tiled<R, G>); }
+template <typename R> cudaError_t set_push_smem(size_t bytes) {
+  const cudaError_t e = raise_smem_limit<push_tiled_fn<R, false>>(bytes);
+  return e != cudaSuccess ? e : raise_smem_limit<push_tiled_fn<R, true>>(bytes);
+}
 
 #define HFF_INST(R)                                                                         \
   template size_t push_tiled_smem<R>(const Params<R> &, int);                               \
   template void launch_push_tail<R>(const Params<R> &, cudaStream_t, int);                  \
-  template void launch_push_tiled<R>(const Params<R> &, const WorkList &, int, cudaStream_t, int); \
+  template void launch_push_tiled<R>(const Params<R> &, const WorkList &, int, cudaStream_t, int, bool); \
   template void launch_inject<R>(const Params<R> &, cudaStream_t);                          \
   template void launch_step_done<R>(const Params<R> &, cudaStream_t);                       \
   template cudaError_t set_push_smem<R>(size_t);

@@ -203,6 +203,33 @@ __global__ void __launch_bounds__(256) k_gather(Species<R> src, Species<R> dst, 
   }
 }
 
+// the count and the removed slots of a sort whose payload moves later
+__global__ void __launch_bounds__(256) k_finish(int32_t *dst_cell, const uint32_t *keys, uint32_t dead, int64_t n,
+                                                long long *count, long long *count_sorted, int species) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    if (keys[q] == dead) {
+      if (q == 0 || keys[q - 1] != dead) { count[species] = q; count_sorted[species] = q; }
+      dst_cell[q] = -1;
+      continue;
+    }
+    if (q == n - 1) { count[species] = n; count_sorted[species] = n; }
+  }
+}
+
+// the deferred payload gather: slots below the (already compacted) count
+template <typename R>
+__global__ void __launch_bounds__(256) k_gather_live(Species<R> src, Species<R> dst, const uint32_t *idx,
+                                                     const long long *count, int species) {
+  const int64_t n = count[species];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = idx[q];
+    dst.cell[q] = src.cell[k];
+    dst.xo[q] = src.xo[k]; dst.yo[q] = src.yo[k];
+    dst.ur[q] = src.ur[k]; dst.ut[q] = src.ut[k]; dst.up[q] = src.up[k];
+    dst.w[q] = src.w[k];
+  }
+}
+
 __global__ void k_set_count(long long *count, long long *count_sorted, int species, long long v) {
   count[species] = v;
   count_sorted[species] = v;
@@ -257,7 +284,8 @@ static int bits_for(uint32_t v) {
 }
 
 template <typename R>
-void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortScratch &ss, cudaStream_t st) {
+void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortScratch &ss, cudaStream_t st,
+                         bool gather) {
   // The slot count lives on the device, so (to stay capturable in a CUDA
   // graph) the passes run over the whole capacity; every slot at or past the
   // count holds cell = -1 (kept so by hff_init, this gather and injection),
@@ -281,7 +309,9 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
     a.first = (pass == 0);
     a.shift = 8 * pass;
     a.keys_in = ki; a.idx_in = ii;
-    a.keys_out = ko; a.idx_out = io;
+    a.keys_out = ko;
+    // the last pass leaves the sorted order in this species' own buffer
+    a.idx_out = (pass == passes - 1) ? const_cast<uint32_t *>(p.sidx[s]) : io;
     k_hist<<<nb, kSortThreads, 0, st>>>(a);
     k_scan_sums<<<nparts, 1024, 0, st>>>(ss.hist, hn, ss.part);
     k_scan_parts<<<1, 1024, 0, st>>>(ss.part, nparts);
@@ -290,12 +320,18 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
     uint32_t *t = ki; ki = ko; ko = t;
     t = ii; ii = io; io = t;
   }
-  // ki / ii now hold the sorted keys and indices
+  // ki holds the sorted keys, p.sidx[s] the sorted order
   k_set_count<<<1, 1, 0, st>>>(p.count, p.count_sorted, s, (long long)n);
-  k_gather<R><<<1216, 256, 0, st>>>(p.sp[s], dst, ii, ki, dead, n, p.count, p.count_sorted, s);
+  if (gather) k_gather<R><<<1216, 256, 0, st>>>(p.sp[s], dst, p.sidx[s], ki, dead, n, p.count, p.count_sorted, s);
+  else k_finish<<<1216, 256, 0, st>>>(dst.cell, ki, dead, n, p.count, p.count_sorted, s);
   cudaMemsetAsync(ss.tile_start, 0, sizeof(int) * (ss.ntiles + 1), st);
   cudaMemsetAsync(ss.tile_end, 0, sizeof(int) * (ss.ntiles + 1), st);
   k_bounds<<<1216, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
+}
+
+template <typename R>
+void launch_materialize(const Params<R> &p, int s, cudaStream_t st) {
+  k_gather_live<R><<<1216, 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
 }
 
 template <typename R>
@@ -306,7 +342,8 @@ void launch_worklist(const Params<R> &p, const SortScratch *ss, const WorkList &
 }
 
 #define HFF_INST(R)                                                                                   \
-  template void launch_sort_species<R>(const Params<R> &, int, Species<R>, const SortScratch &, cudaStream_t); \
+  template void launch_sort_species<R>(const Params<R> &, int, Species<R>, const SortScratch &, cudaStream_t, bool); \
+  template void launch_materialize<R>(const Params<R> &, int, cudaStream_t); \
   template void launch_worklist<R>(const Params<R> &, const SortScratch *, const WorkList &, int, int,   \
                                    cudaStream_t);
 HFF_INST(float)

@@ -132,3 +132,36 @@ def test_fp32_and_fp64_instances_agree(env):
     assert abs(d32.psi_open - d64.psi_open) < 1e-5 * abs(d64.psi_open)
     for f in FIELDS6:
         assert rel_l2(s32.get(f), s64.get(f)) < 2e-4, f
+
+
+def test_deferred_gather_same_state(env):
+    """A sort leaves its payload gather to the next push; reading the
+    particles in between performs the gather eagerly instead.  Both routes
+    give the same state (FP64: up to the rounding of the atomic deposit
+    order)."""
+    hff, workloads, _ = env
+    cfg = workloads.config("small_pic")
+    cfg.update(capacity=40000, sort_every=4, precision="fp64")
+    ps = workloads.particles(cfg, n_pairs=6000, seed=41)
+    runs = []
+    for mode in ("straight", "read", "diag"):
+        sim = hff.Sim(cfg)
+        for s in range(2):
+            sim.load(s, ps[s])
+        sim.step(4)                       # ends with a sort: gather pending
+        if mode == "read":
+            sim.particles(1)
+        elif mode == "diag":
+            sim.diagnostics()
+        sim.step(5)
+        runs.append(({s: sim.particles(s) for s in range(2)}, {f: sim.get(f) for f in ("E_r", "E_ph", "B_th")}))
+        assert sim.status() == 0
+        sim.close()
+    ref_p, ref_f = runs[0]
+    for parts, fields in runs[1:]:
+        for s in range(2):
+            assert np.array_equal(parts[s]["cell"], ref_p[s]["cell"])
+            for k in ("xo", "yo", "ur", "ut", "up", "w"):
+                np.testing.assert_allclose(parts[s][k], ref_p[s][k], rtol=1e-12, atol=1e-14)
+        for f in fields:
+            np.testing.assert_allclose(fields[f], ref_f[f], rtol=1e-11, atol=1e-14)
