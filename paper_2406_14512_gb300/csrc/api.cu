@@ -962,7 +962,7 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
   if (nsm <= 0) nsm = 1;
   h->tail_grid = nsm * 4;
   {
-    const size_t psm = (size_t)(cfg->nt + 1) * (cfg->precision == HFF_FP64 ? 8 : 4);
+    const size_t psm = cfg->precision == HFF_FP64 ? psi_smem<double>(cfg->nt) : psi_smem<float>(cfg->nt);
     const cudaError_t e = cfg->precision == HFF_FP64 ? set_psi_smem<double>(psm) : set_psi_smem<float>(psm);
     if (e != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the flux-prefix shared memory size"));
   }

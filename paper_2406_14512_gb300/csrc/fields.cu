@@ -25,8 +25,12 @@ constexpr int kRowThreads = 128;
 // the row is staged through shared memory (coalesced in and out), each
 // thread sums a contiguous chunk serially in FP64 (one conversion and one
 // add per element), one block-wide scan of the chunk totals gives the
-// offsets, and the prefix is rounded to the working precision.
+// offsets, and the prefix is rounded to the working precision.  The staged
+// row is padded by one word every 32 (element j at j + j/32), so that the
+// threads of a warp, each walking its own contiguous chunk, hit distinct
+// banks.
 constexpr int kPsiThreads = 256;
+__host__ __device__ __forceinline__ int psi_pad(int j) { return j + (j >> 5); }
 
 template <typename R>
 __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
@@ -36,12 +40,12 @@ __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   const int i = blockIdx.x, nt = p.nt, tid = threadIdx.x;
   const R *br = p.f.br + (int64_t)i * nt;
   const R *br0 = p.f.br0 + (int64_t)i * nt;
-  for (int j = tid; j < nt; j += kPsiThreads) row[j] = (br0[j] + br[j]) * (R)p.t.dcp[j];
+  for (int j = tid; j < nt; j += kPsiThreads) row[psi_pad(j)] = (br0[j] + br[j]) * (R)p.t.dcp[j];
   __syncthreads();
   const int chunk = (nt + kPsiThreads - 1) / kPsiThreads;
   const int j0 = min(tid * chunk, nt), j1 = min(j0 + chunk, nt);
   double acc = 0.0;
-  for (int j = j0; j < j1; ++j) acc += (double)row[j];
+  for (int j = j0; j < j1; ++j) acc += (double)row[psi_pad(j)];
   // exclusive scan of the chunk totals over the block
   const int lane = tid & 31, wid = tid >> 5;
   double x = acc;
@@ -56,15 +60,15 @@ __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   const double r2 = p.t.r2n[i];
   // rewrite the chunk in place with the prefix (inclusive, shifted by one)
   double run = off;
-  R prev = (j0 < j1) ? row[j0] : R(0);
+  R prev = (j0 < j1) ? row[psi_pad(j0)] : R(0);
   for (int j = j0; j < j1; ++j) {
     run += (double)prev;
-    prev = (j + 1 < j1) ? row[j + 1] : R(0);
-    row[j] = (R)(r2 * run);  // becomes Psi(i, j+1)
+    prev = (j + 1 < j1) ? row[psi_pad(j + 1)] : R(0);
+    row[psi_pad(j)] = (R)(r2 * run);  // becomes Psi(i, j+1)
   }
   __syncthreads();
   R *psi = p.f.psi + (int64_t)i * (nt + 1);
-  for (int j = tid; j <= nt; j += kPsiThreads) psi[j] = (j == 0) ? R(0) : row[j - 1];
+  for (int j = tid; j <= nt; j += kPsiThreads) psi[j] = (j == 0) ? R(0) : row[psi_pad(j - 1)];
 }
 
 // ----------------------------------------------------------- collocation
@@ -299,8 +303,9 @@ __global__ void k_bc(Params<R> p) {
 
 static inline dim3 row_grid(int rows, int nt) { return dim3((nt + 1 + kRowThreads - 1) / kRowThreads, rows); }
 
+template <typename R> size_t psi_smem(int nt) { return (size_t)(psi_pad(nt) + 2) * sizeof(R); }
 template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s) {
-  const size_t smem = (size_t)(p.nt + 1) * sizeof(R);
+  const size_t smem = psi_smem<R>(p.nt);
   k_psi<R><<<p.nr + 1, kPsiThreads, smem, s>>>(p);
 }
 template <typename R> const void *psi_fn() { return reinterpret_cast<const void *>(&k_psi<R>); }
@@ -338,6 +343,7 @@ template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_
   template void launch_combine<R>(R *, const R *, const R *, int64_t, int, cudaStream_t); \
   template void launch_psi<R>(const Params<R> &, cudaStream_t);                \
   template cudaError_t set_psi_smem<R>(size_t);                                \
+  template size_t psi_smem<R>(int);                                            \
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \

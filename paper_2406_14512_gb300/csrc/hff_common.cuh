@@ -157,6 +157,7 @@ __device__ __forceinline__ int64_t ix(int i, int j, int ld) { return (int64_t)i 
 // launchers (defined in fields.cu / particles.cu / sort.cu / diag.cu)
 template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s);
 template <typename R> cudaError_t set_psi_smem(size_t bytes);
+template <typename R> size_t psi_smem(int nt);  // dynamic shared memory of the flux prefix
 template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s);
 template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);

@@ -50,9 +50,14 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+  const int lane = threadIdx.x & 31;
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t e = base + r * kSortThreads + threadIdx.x;
-    if (e < a.n) atomicAdd(&h[(load_key(a, e) >> a.shift) & 255u], 1u);
+    // nearly sorted input puts most of a warp on one digit: one shared
+    // atomic per distinct digit of the warp
+    const uint32_t d = (e < a.n) ? ((load_key(a, e) >> a.shift) & 255u) : 256u;
+    const unsigned same = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && lane == __ffs(same) - 1) atomicAdd(&h[d], (uint32_t)__popc(same));
   }
   __syncthreads();
   a.hist[(int64_t)threadIdx.x * a.nb + blockIdx.x] = h[threadIdx.x];
@@ -277,6 +282,13 @@ __global__ void __launch_bounds__(1024) k_worklist(const int *start, const int *
   if (threadIdx.x == 0) *n_items = (int)min((int)carry, max_items);
 }
 
+// blocks of 256 threads for one thread per element (the kernels keep a
+// grid-stride loop, so the cap only matters beyond 2^39 elements)
+static unsigned one_per_thread(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : (b > 0x7fffffff ? 0x7fffffff : b));
+}
+
 static int bits_for(uint32_t v) {
   int b = 0;
   while ((1ull << b) <= v) ++b;
@@ -322,16 +334,18 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
   }
   // ki holds the sorted keys, p.sidx[s] the sorted order
   k_set_count<<<1, 1, 0, st>>>(p.count, p.count_sorted, s, (long long)n);
-  if (gather) k_gather<R><<<1216, 256, 0, st>>>(p.sp[s], dst, p.sidx[s], ki, dead, n, p.count, p.count_sorted, s);
-  else k_finish<<<1216, 256, 0, st>>>(dst.cell, ki, dead, n, p.count, p.count_sorted, s);
+  // one thread per slot: enough loads in flight to cover DRAM latency
+  const unsigned g1 = one_per_thread(n);
+  if (gather) k_gather<R><<<g1, 256, 0, st>>>(p.sp[s], dst, p.sidx[s], ki, dead, n, p.count, p.count_sorted, s);
+  else k_finish<<<g1, 256, 0, st>>>(dst.cell, ki, dead, n, p.count, p.count_sorted, s);
   cudaMemsetAsync(ss.tile_start, 0, sizeof(int) * (ss.ntiles + 1), st);
   cudaMemsetAsync(ss.tile_end, 0, sizeof(int) * (ss.ntiles + 1), st);
-  k_bounds<<<1216, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
+  k_bounds<<<g1, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
 }
 
 template <typename R>
 void launch_materialize(const Params<R> &p, int s, cudaStream_t st) {
-  k_gather_live<R><<<1216, 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
+  k_gather_live<R><<<one_per_thread(p.cap), 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
 }
 
 template <typename R>
