@@ -123,6 +123,12 @@ typedef struct hff_config {
   int32_t tile_r, tile_t;   /* sort tile in cells (0 = default 16 x 32)          */
   int32_t sort_every;       /* sort cadence in steps, 1..8 (0 = never sort)      */
   int32_t precision;        /* HFF_FP32 or HFF_FP64                              */
+  double gamma_th;          /* threshold pair creation (Sect. 5.1): a lepton whose
+                               Lorentz factor exceeds gamma_th after its push
+                               creates an e+- pair (0 = off, else > 1)           */
+  double gamma_s;           /* Lorentz factor of each created particle (>= 1);
+                               both move along the parent's direction, at its
+                               position, with its weight; the parent is kept     */
 } hff_config;
 
 typedef struct hff_info {
@@ -154,6 +160,7 @@ typedef struct hff_diag {
   double kinetic[4];        /* sum w m (gamma - 1) per species                   */
   double count[4];          /* live particles per species                        */
   double injected, killed, radiated, nonfinite; /* running totals (weights)      */
+  double created;           /* weight of the created pairs (both species)        */
 } hff_diag;
 
 typedef struct hff_handle hff_handle;

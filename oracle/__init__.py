@@ -42,6 +42,7 @@ class _Cfg(C.Structure):
         ("shell_r", C.c_double), ("synth_psi_open", C.c_double),
         ("seed", C.c_uint64), ("capacity", C.c_int64),
         ("tile_r", C.c_int32), ("tile_t", C.c_int32), ("sort_every", C.c_int32),
+        ("gamma_th", C.c_double), ("gamma_s", C.c_double),
     ]
 
 
@@ -52,14 +53,15 @@ class Diag(C.Structure):
         ("rho_max", C.c_double), ("u_e", C.c_double), ("u_b", C.c_double),
         ("kinetic", C.c_double * 4), ("count", C.c_double * 4),
         ("injected", C.c_double), ("killed", C.c_double), ("radiated", C.c_double),
-        ("nonfinite", C.c_double),
+        ("nonfinite", C.c_double), ("created", C.c_double),
     ]
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (plain C11, -O2, no -march)."""
     with _lock:
-        if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.join(os.path.dirname(_SRC), "hff_oracle.h")))
+        if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
             os.makedirs(os.path.dirname(_OUT), exist_ok=True)
             tmp = _OUT + f".{os.getpid()}.tmp"
             subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp,
@@ -141,6 +143,8 @@ def _cfg_struct(cfg: dict) -> _Cfg:
     c.capacity = int(cfg.get("capacity", 0))
     c.tile_r, c.tile_t = int(cfg.get("tile_r", 16)), int(cfg.get("tile_t", 16))
     c.sort_every = int(cfg.get("sort_every", 0))
+    c.gamma_th = float(cfg.get("gamma_th", 0.0))
+    c.gamma_s = float(cfg.get("gamma_s", 0.0))
     return c
 
 

@@ -22,7 +22,8 @@
  *   5. correction  : node pass B renormalises the collocated E^{n+1} against
  *                    B^{n+1/2} (Eqs. 25-26); E += f <Delta E> on the mesh
  *   6. Faraday     : B^{n+1/2} -> B^{n+1} from the corrected E, absorber on B
- *   7. injection   : top-up of the surface pair density (Sects. 4, 5.1)
+ *   7. injection   : top-up of the surface pair density (Sects. 4, 5.1),
+ *                    then the pairs of the threshold pair creation (Sect. 5.1)
  *   8. sort        : stable sort by tile key with compaction, every k steps
  *
  * Parity pins for each part live in tests/test_oracle_*.py.  Parity unpinned:
@@ -49,7 +50,12 @@ typedef struct {
   int32_t *surf, *target;
   int64_t step;
   double rr_k[4];
-  double injected, killed, radiated, nonfinite;
+  double injected, killed, radiated, nonfinite, created;
+  /* pair-creation events of the current step, in push order (species 0 by
+   * particle index, then species 1): new cell, offsets, momentum, weight   */
+  int64_t n_ev, cap_ev;
+  int32_t *ev_cell;
+  double *ev[6];
 } ost;
 
 /* ------------------------------------------------------------------ sizes */
@@ -291,6 +297,9 @@ void *or_create(const or_config *cfg) {
    * fixed once.                                                               */
   s->surf = (int32_t *)calloc(s->nt, sizeof(int32_t));
   s->target = (int32_t *)calloc(s->nt, sizeof(int32_t));
+  s->cap_ev = s->cap > 0 ? s->cap : 1;
+  s->ev_cell = (int32_t *)calloc(s->cap_ev, sizeof(int32_t));
+  for (int k = 0; k < 6; ++k) s->ev[k] = (double *)calloc(s->cap_ev, sizeof(double));
   {
     double pacc = 0.0, r0 = rn(s, 0);
     for (int j = 0; j < s->nt; ++j) {
@@ -320,6 +329,8 @@ void or_destroy(void *st) {
   }
   free(s->surf);
   free(s->target);
+  free(s->ev_cell);
+  for (int k = 0; k < 6; ++k) free(s->ev[k]);
   free(s);
 }
 
@@ -644,6 +655,7 @@ static void push_all(ost *s) {
   int nr = s->nr, nt = s->nt;
   (void)nr;
   memset(s->surf, 0, sizeof(int32_t) * nt);
+  s->n_ev = 0;
   double dt = s->dt;
   for (int sp = 0; sp < s->c.n_species; ++sp) {
     double qm = s->c.q[sp] / s->c.m[sp], krr = s->rr_k[sp] * s->c.rr_scale;
@@ -702,8 +714,35 @@ static void push_all(ost *s) {
       xo[p] = xn; yo[p] = yn;
       ur[p] = uo[0]; ut[p] = uo[1]; up[p] = uo[2];
       if (i1 == 0) s->surf[j1] += 1;
+      /* Sect. 5.1: a lepton above the threshold Lorentz factor creates a pair
+       * at its position, moving along its direction with gamma_s; the parent
+       * is left as it is (reading), at most one pair per parent and step.    */
+      if (s->c.gamma_th > 0 && sp < 2 && 1.0 + dot(uo, uo) > s->c.gamma_th * s->c.gamma_th) {
+        if (s->n_ev >= s->cap_ev) { fprintf(stderr, "oracle: pair event capacity exceeded\n"); abort(); }
+        double a = sqrt(s->c.gamma_s * s->c.gamma_s - 1.0) / sqrt(dot(uo, uo));
+        int64_t e = s->n_ev++;
+        s->ev_cell[e] = cell[p];
+        s->ev[0][e] = xn; s->ev[1][e] = yn;
+        s->ev[2][e] = a * uo[0]; s->ev[3][e] = a * uo[1]; s->ev[4][e] = a * uo[2];
+        s->ev[5][e] = w[p];
+      }
     }
   }
+}
+
+/* The pairs of this step's creation events, appended to species 0 (e-) and
+ * 1 (e+) in event order after the injected ones.                           */
+static void create_pairs(ost *s) {
+  if (s->c.n_species < 2) { s->n_ev = 0; return; }
+  for (int64_t e = 0; e < s->n_ev; ++e)
+    for (int sp = 0; sp < 2; ++sp) {
+      if (s->n[sp] >= s->cap) { fprintf(stderr, "oracle: particle capacity exceeded\n"); abort(); }
+      int64_t p = s->n[sp]++;
+      s->cell[sp][p] = s->ev_cell[e];
+      for (int k = 0; k < 6; ++k) s->p[sp][k][p] = s->ev[k][e];
+      s->created += s->ev[5][e];
+    }
+  s->n_ev = 0;
 }
 
 /* ----------------------------------------------------------- 4/6. Faraday
@@ -873,7 +912,7 @@ int or_step(void *st, int32_t nsteps, int32_t stages) {
     if (stages & OR_ST_AMPERE) ampere(s);
     if (stages & OR_ST_CORRECT) correct_e(s);
     if (stages & OR_ST_FARADAY2) { faraday(s, 0.5); absorb_b(s); }
-    if (stages & OR_ST_INJECT) inject(s);
+    if (stages & OR_ST_INJECT) { inject(s); create_pairs(s); }
     s->step++;
     if ((stages & OR_ST_SORT) && s->c.sort_every > 0 && s->step % s->c.sort_every == 0)
       for (int sp = 0; sp < s->c.n_species; ++sp) sort_species(s, sp);
@@ -992,5 +1031,6 @@ int or_diagnostics(void *st, or_diag *o, double *lprof) {
   o->killed = s->killed;
   o->radiated = s->radiated;
   o->nonfinite = s->nonfinite;
+  o->created = s->created;
   return 0;
 }

@@ -76,6 +76,8 @@ typedef struct or_config {
   int64_t capacity;          /* particles per species                        */
   int32_t tile_r, tile_t;    /* sort tile shape in cells                     */
   int32_t sort_every;        /* sort cadence in steps (0 = never)            */
+  double gamma_th;           /* pair creation threshold (0 = off), Sect. 5.1 */
+  double gamma_s;            /* Lorentz factor of the created pairs          */
 } or_config;
 
 typedef struct or_diag {
@@ -87,6 +89,7 @@ typedef struct or_diag {
   double kinetic[4];         /* sum w m (gamma - 1) per species              */
   double count[4];
   double injected, killed, radiated, nonfinite;
+  double created;            /* weight of the pairs created (both species)   */
 } or_diag;
 
 void *or_create(const or_config *cfg);

@@ -118,6 +118,9 @@ int validate(const hff_config *c) {
   if (!(c->r_abs > c->r_min) || xi_abs > c->nr - 3) return fail(HFF_ERR_ARG, "r_abs must lie >= 3 cells inside r_max");
   if (c->tile_r < 0 || c->tile_t < 0 || c->tile_r > 64 || c->tile_t > 128)
     return fail(HFF_ERR_ARG, "tile out of range");
+  if (!(c->gamma_th == 0 || c->gamma_th > 1) || (c->gamma_th > 0 && !(c->gamma_s >= 1.0)))
+    return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
+  if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
   return HFF_OK;
 }
 
@@ -145,6 +148,8 @@ struct Offsets {
   size_t sidx[kMaxSpecies];  // sorted order of the last sort, per species
   size_t items;
   size_t qnode, rows, psi64;
+  size_t ev[8];          // pair-creation events: key cell xo yo ur ut up w
+  int64_t ev_cap;
   int ntiles, ntt, max_items, nb, nparts;
   size_t total;
 };
@@ -154,7 +159,8 @@ struct Small {  // device counters, one 256-byte block
   long long count_sorted[kMaxSpecies];
   long long inj_base[kMaxSpecies];
   long long step;
-  double acc[4];
+  double acc[5];              // injected, killed, radiated, nonfinite, created
+  unsigned pe_count;          // pair-creation events of the current step
   double rr;
   double kin[kMaxSpecies];
   double cnt[kMaxSpecies];
@@ -213,6 +219,9 @@ void layout(const hff_config &c, Offsets &o) {
     o.tend = L.take(((size_t)o.ntiles + 1) * 4);
     o.items = L.take((size_t)o.max_items * sizeof(int4));
   }
+  // pair-creation events of one step (bounded; overflow is latched)
+  o.ev_cap = c.gamma_th > 0 ? cap / 4 + 1024 : 0;
+  for (int k = 0; k < 8; ++k) o.ev[k] = o.ev_cap ? L.take((size_t)o.ev_cap * (k < 2 ? 4 : R)) : 0;
   o.qnode = L.take(nn * 8);
   o.rows = L.take((nr + 1) * 8 * 8);
   o.psi64 = L.take(nn * 8);
@@ -347,6 +356,17 @@ void fill_params(hff_handle *h) {
     p.pushed = h->small->pushed;
     p.status = &h->small->status;
     p.tile_r = tile_r_of(c); p.tile_t = tile_t_of(c); p.ntt = o.ntt;
+    p.pairs = c.gamma_th > 0 ? 1 : 0;
+    p.gamma_th2 = (R)(c.gamma_th * c.gamma_th);
+    p.u_s = (R)std::sqrt(c.gamma_s > 1 ? c.gamma_s * c.gamma_s - 1.0 : 0.0);
+    p.pe_count = &h->small->pe_count;
+    p.pe_cap = o.ev_cap;
+    if (o.ev_cap) {
+      p.ev_key = reinterpret_cast<uint32_t *>(b + o.ev[0]);
+      p.ev_cell = reinterpret_cast<int32_t *>(b + o.ev[1]);
+      R **e[6] = {&p.ev_xo, &p.ev_yo, &p.ev_ur, &p.ev_ut, &p.ev_up, &p.ev_w};
+      for (int k = 0; k < 6; ++k) *e[k] = reinterpret_cast<R *>(b + o.ev[k + 2]);
+    }
   }
 }
 
@@ -532,6 +552,8 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
   }
   if ((parts & 1) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
     CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
+  if ((parts & 1) && (stages & HFF_ST_PUSH) && h->c.gamma_th > 0)  // events of this step only
+    CK(cudaMemsetAsync(&h->small->pe_count, 0, sizeof(unsigned), s));
   if ((parts & 2) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
     launch_push_tiled<R>(p, h->wl, h->halo, s, h->push_grid, gather);
   if (!(parts & 4)) {
@@ -1219,6 +1241,7 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
   out->killed = sm.acc[1];
   out->radiated = sm.acc[2];
   out->nonfinite = sm.acc[3];
+  out->created = sm.acc[4];
   return HFF_OK;
 }
 

@@ -122,6 +122,15 @@ struct Params {
   unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel
   unsigned *status;
   int tile_r, tile_t, ntt;  // sort tiles
+  // threshold pair creation (Sect. 5.1): events recorded by the push, the
+  // pairs appended after the injection
+  int pairs;
+  R gamma_th2, u_s;         // gamma_th^2, |u| of a created particle
+  unsigned *pe_count;
+  int64_t pe_cap;
+  uint32_t *ev_key;         // (species << 31) | parent slot: the append order
+  int32_t *ev_cell;
+  R *ev_xo, *ev_yo, *ev_ur, *ev_ut, *ev_up, *ev_w;
 };
 
 // piecewise-linear blend f(Psi) of Eqs. 29-31 (right-continuous at jumps)

@@ -418,10 +418,32 @@ struct SpeciesConst {
   Species<R> S, In;
   const uint32_t *sidx;
   R qm, krr, q, m;
+  uint32_t key_hi;   // species in the top bit of a pair-creation event key
+  bool creates;      // a lepton of a run with pair creation
   __device__ __forceinline__ SpeciesConst(const Params<R> &p, int s, bool gather = false)
       : S(p.sp[s]), In(gather ? p.src[s] : p.sp[s]), sidx(p.sidx[s]), qm(p.qm[s]),
-        krr(p.krr[s] * (R)(*p.rr_scale)), q(p.q[s]), m(p.m[s]) {}
+        krr(p.krr[s] * (R)(*p.rr_scale)), q(p.q[s]), m(p.m[s]), key_hi((uint32_t)s << 31),
+        creates(p.pairs != 0 && s < 2) {}
 };
+
+// Sect. 5.1: a lepton above the threshold Lorentz factor creates a pair at
+// its new position, along its direction of motion, with gamma_s.  Recorded
+// as an event here (slot order of the atomic is arbitrary; the key restores
+// the parent order when the pairs are appended).
+template <typename R>
+__device__ __forceinline__ void record_pair(const Params<R> &p, const SpeciesConst<R> &K, int q, int cell, R xn,
+                                            R yn, const R uo[3], R w) {
+  const R u2 = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
+  if (!(R(1) + u2 > p.gamma_th2)) return;
+  const unsigned e = atomicAdd(p.pe_count, 1u);
+  if ((int64_t)e >= p.pe_cap) { atomicOr(p.status, kStCapacity); return; }
+  const R a = p.u_s * rsq(u2);
+  p.ev_key[e] = K.key_hi | (uint32_t)q;
+  p.ev_cell[e] = cell;
+  p.ev_xo[e] = xn; p.ev_yo[e] = yn;
+  p.ev_ur[e] = a * uo[0]; p.ev_ut[e] = a * uo[1]; p.ev_up[e] = a * uo[2];
+  p.ev_w[e] = w;
+}
 
 // One particle: gather, push, move, kill rules, deposit, store.  Reads
 // particle qi of K.In and writes slot q of K.S (the same particle unless the
@@ -498,6 +520,7 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
   S.ur[q] = uo[0]; S.ut[q] = uo[1]; S.up[q] = uo[2];
   if constexpr (kGather) S.w[q] = w;
   if (i1 == 0 && p.inject) atomicAdd(&p.surf[j1], 1);
+  if (K.creates) record_pair(p, K, q, i1 * nt + j1, xn, yn, uo, w);
 }
 
 // out-of-region fallback of the tiled kernel (kept out of line so that the
@@ -744,6 +767,59 @@ __global__ void __launch_bounds__(128) k_inject_write(Params<R> p) {
   }
 }
 
+// The pairs of this step's events, appended to species 0 and 1 after the
+// injected particles, in parent order (species 0 by slot, then species 1):
+// each event is ranked by counting the smaller keys, for up to kRankMax
+// events (a larger number, far beyond the parity cases, keeps the arbitrary
+// event order).  One block.
+constexpr int kRankMax = 4096;
+template <typename R>
+__global__ void __launch_bounds__(1024) k_pairs_append(Params<R> p) {
+  __shared__ uint32_t skey[kRankMax];
+  __shared__ long long base[2];
+  __shared__ double wsum[32];
+  const unsigned n_raw = *p.pe_count;
+  const int64_t n = (int64_t)n_raw < p.pe_cap ? (int64_t)n_raw : p.pe_cap;
+  const bool ranked = n <= kRankMax;
+  if (threadIdx.x < 2) base[threadIdx.x] = p.count[threadIdx.x];
+  if (ranked)
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) skey[e] = p.ev_key[e];
+  __syncthreads();
+  double ws = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    int64_t rank = e;
+    if (ranked) {
+      const uint32_t k = skey[e];
+      rank = 0;
+      for (int64_t f = 0; f < n; ++f) rank += skey[f] < k;
+    }
+    ws += (double)p.ev_w[e];
+    for (int s = 0; s < 2; ++s) {
+      const int64_t q = base[s] + rank;
+      if (q >= p.cap) continue;
+      Species<R> S = p.sp[s];
+      S.cell[q] = p.ev_cell[e];
+      S.xo[q] = p.ev_xo[e]; S.yo[q] = p.ev_yo[e];
+      S.ur[q] = p.ev_ur[e]; S.ut[q] = p.ev_ut[e]; S.up[q] = p.ev_up[e];
+      S.w[q] = p.ev_w[e];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) ws += __shfl_down_sync(0xffffffffu, ws, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+    for (int s = 0; s < 2; ++s) {
+      long long end = base[s] + n;
+      if (end > p.cap) { end = p.cap; atomicOr(p.status, kStCapacity); }
+      p.count[s] = end;
+    }
+    p.acc[4] += 2.0 * t;
+    *p.pe_count = 0u;
+  }
+}
+
 template <typename R>
 __global__ void k_step_done(Params<R> p) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *p.step += 1;
@@ -754,6 +830,7 @@ template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s) {
     k_inject_scan<R><<<1, 1024, 0, s>>>(p);
     k_inject_write<R><<<(p.nt + 127) / 128, 128, 0, s>>>(p);
   }
+  if (p.pairs) k_pairs_append<R><<<1, 1024, 0, s>>>(p);
   k_step_done<R><<<1, 32, 0, s>>>(p);
 }
 template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s) {

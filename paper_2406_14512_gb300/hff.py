@@ -46,6 +46,7 @@ class hff_config(C.Structure):
         ("shell_r", C.c_double), ("synth_psi_open", C.c_double), ("seed", C.c_uint64),
         ("capacity", C.c_int64), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
         ("sort_every", C.c_int32), ("precision", C.c_int32),
+        ("gamma_th", C.c_double), ("gamma_s", C.c_double),
     ]
 
 
@@ -68,7 +69,8 @@ class hff_diag(C.Structure):
                 ("l_out", C.c_double), ("gauss_max", C.c_double), ("gauss_rms", C.c_double),
                 ("rho_max", C.c_double), ("u_e", C.c_double), ("u_b", C.c_double),
                 ("kinetic", C.c_double * 4), ("count", C.c_double * 4), ("injected", C.c_double),
-                ("killed", C.c_double), ("radiated", C.c_double), ("nonfinite", C.c_double)]
+                ("killed", C.c_double), ("radiated", C.c_double), ("nonfinite", C.c_double),
+                ("created", C.c_double)]
 
 
 _lib = None
@@ -152,6 +154,8 @@ def config_struct(cfg: dict) -> hff_config:
     c.tile_r, c.tile_t = int(cfg.get("tile_r", 16)), int(cfg.get("tile_t", 32))
     c.sort_every = int(cfg.get("sort_every", 0))
     c.precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
+    c.gamma_th = float(cfg.get("gamma_th", 0.0))
+    c.gamma_s = float(cfg.get("gamma_s", 0.0))
     return c
 
 

@@ -61,7 +61,7 @@ def _base(nr, nt, r_max, r_lc, geom, kappa=10.0, ppc_inj=4.0, courant=0.5, seed=
                 q=[-1.0, 1.0], m=[m_e, m_e], inject=True, kappa_inj=kappa, w_inj=w_inj,
                 gamma_rad=0.0, b_ref=1.0 / r_lc ** 3, rr_scale=1.0, shell_r=2.0 * r_min,
                 synth_psi_open=1.25, seed=seed, capacity=0, tile_r=16, tile_t=32,
-                sort_every=8, dt_estimate=dt)
+                sort_every=8, dt_estimate=dt, gamma_th=0.0, gamma_s=0.0)
 
 
 def config(name: str) -> dict:
@@ -101,6 +101,13 @@ def config(name: str) -> dict:
             c = _base(200, 120, 20.0, 4.0, "synth", seed=15)
             c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=8000,
                      steps=10, precision="fp32", place="band", sheet_frac=0.2, momenta="powerlaw")
+            c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
+        elif kind == "pairs":    # PIC everywhere with threshold pair creation (Sect. 5.1)
+            c = _base(72, 56, 30.0, 3.0, "dipole", seed=16)
+            # gamma ~ gamma^-2 up to 1e6, so about 2% of the leptons start above
+            # gamma_th; gamma_th / gamma_s = 1e6 / 2.2e5 as in Table 1
+            c.update(n_pairs=4000, steps=10, precision="fp32", place="uniform", momenta="powerlaw",
+                     gamma_th=50.0, gamma_s=50.0 * 2.2e5 / 1e6)
             c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
         elif kind == "michel":   # monopole, south hemisphere force-free (Sect. 4)
             c = _base(64, 64, 50.0 / 3.0, 5.0, "michel", seed=14)
