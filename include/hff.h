@@ -255,6 +255,41 @@ int hff_destroy(hff_handle *h);
 /* Message of the last error on this thread ("" if none). */
 const char *hff_last_error(void);
 
+/* Maps of one species for the density and energy figures of Sect. 5.2, in
+ * FP64 on the host (nr x nt each, theta fastest; either may be NULL): the
+ * number density sum(w) / V_cell and the kinetic energy density
+ * sum(w m (gamma - 1)) / V_cell of the live particles, V_cell the exact cell
+ * volume.  Synchronises the stream. */
+int hff_species_maps(hff_handle *h, int inst, int species, double *density, double *energy);
+
+/* Energy spectrum of one species (Sect. 5.2): the weights of its live
+ * particles in nbins (1..4096) bins uniform in log10(gamma) over
+ * [lg_min, lg_max); particles outside fall into the end bins.  out: nbins
+ * doubles on the host.  Synchronises the stream. */
+int hff_spectrum(hff_handle *h, int inst, int species, int nbins, double lg_min, double lg_max, double *out);
+
+/* ---------------------------------------------------------------------------
+ * Checkpoint and resume of one instance (`inst` of an ensemble), in host
+ * memory.  The blob holds the configuration, the step counter, the running
+ * totals, E and B - B_0, and the live particles of every species.  Taking
+ * the size or saving first sorts the particles by tile (a reordering that
+ * changes no physical quantity), so that a resumed run starts from exactly
+ * the state the saving run continues from; the injection generator is keyed
+ * by (seed, step), so both inject the same particles.  Two runs still differ
+ * by the summation order of the atomic deposit (rounding only).
+ *
+ * hff_checkpoint_size: bytes of the blob for the current state (synchronises).
+ * hff_checkpoint_save: writes the blob to dst (host, >= that size; nothing
+ *   may step the instance in between).  HFF_ERR_CAPACITY if dst is too small.
+ * hff_checkpoint_load: restores a blob into an instance of the same
+ *   configuration (only capacity, which must hold the saved particles, and
+ *   rr_scale may differ; the saved ramp scalar is restored).  HFF_ERR_ARG for
+ *   a foreign, truncated or mismatched blob, HFF_ERR_CAPACITY if the
+ *   particles do not fit.  Synchronises the stream. */
+int hff_checkpoint_size(hff_handle *h, int inst, size_t *bytes);
+int hff_checkpoint_save(hff_handle *h, int inst, void *dst, size_t bytes);
+int hff_checkpoint_load(hff_handle *h, int inst, const void *src, size_t bytes);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free tile ordering.  No counterpart in the paper: this is a
  * service for callers that may not allocate device memory at all -- code

@@ -104,6 +104,8 @@ def lib():
         L.or_sort_now.argtypes = [vp]
         L.or_diagnostics.argtypes = [vp, C.POINTER(Diag), vp]
         L.or_node_charge.argtypes = [vp, vp]
+        L.or_species_maps.argtypes = [vp, C.c_int, vp, vp]
+        L.or_spectrum.argtypes = [vp, C.c_int, C.c_int, d, d, vp]
         L.or_push_local.argtypes = [d, d, d, pd, pd, pd, pd, pd]
         L.or_move_local.argtypes = [d, d, d, pd, pd, pd, pd, pd]
         L.or_blend.restype = d
@@ -242,6 +244,18 @@ class Oracle:
         q = np.empty((self.nr + 1, self.nt + 1), np.float64)
         self.L.or_node_charge(self.h, _ptr(q))
         return q
+
+    def species_maps(self, species: int):
+        """(number density, kinetic energy density) per cell, nr x nt."""
+        d = np.empty((self.nr, self.nt), np.float64)
+        e = np.empty((self.nr, self.nt), np.float64)
+        self.L.or_species_maps(self.h, species, _ptr(d), _ptr(e))
+        return d, e
+
+    def spectrum(self, species: int, nbins: int, lg_min: float, lg_max: float) -> np.ndarray:
+        out = np.empty(nbins, np.float64)
+        self.L.or_spectrum(self.h, species, nbins, lg_min, lg_max, _ptr(out))
+        return out
 
     def blend(self, psi: float) -> float:
         return self.L.or_blend(self.h, psi)

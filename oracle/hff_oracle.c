@@ -920,6 +920,41 @@ int or_step(void *st, int32_t nsteps, int32_t stages) {
   return 0;
 }
 
+/* ------------------------------------------------- maps and spectra (5.2) */
+int or_species_maps(void *st, int sp, double *density, double *energy) {
+  ost *s = (ost *)st;
+  int64_t nc = (int64_t)s->nr * s->nt;
+  for (int64_t c = 0; c < nc; ++c) { density[c] = 0.0; energy[c] = 0.0; }
+  for (int64_t p = 0; p < s->n[sp]; ++p) {
+    int32_t c = s->cell[sp][p];
+    if (c < 0) continue;
+    double u2 = s->p[sp][2][p] * s->p[sp][2][p] + s->p[sp][3][p] * s->p[sp][3][p] + s->p[sp][4][p] * s->p[sp][4][p];
+    double gamma = sqrt(1.0 + u2);
+    density[c] += s->p[sp][5][p];
+    energy[c] += s->p[sp][5][p] * s->c.m[sp] * (gamma - 1.0);
+  }
+  for (int i = 0; i < s->nr; ++i)
+    for (int j = 0; j < s->nt; ++j) {
+      double v = 2.0 * PI / 3.0 * (pow(rn(s, i + 1), 3) - pow(rn(s, i), 3)) * dcp(s, j);
+      density[(int64_t)i * s->nt + j] /= v;
+      energy[(int64_t)i * s->nt + j] /= v;
+    }
+  return 0;
+}
+
+int or_spectrum(void *st, int sp, int nbins, double lg_min, double lg_max, double *out) {
+  ost *s = (ost *)st;
+  for (int b = 0; b < nbins; ++b) out[b] = 0.0;
+  for (int64_t p = 0; p < s->n[sp]; ++p) {
+    if (s->cell[sp][p] < 0) continue;
+    double u2 = s->p[sp][2][p] * s->p[sp][2][p] + s->p[sp][3][p] * s->p[sp][3][p] + s->p[sp][4][p] * s->p[sp][4][p];
+    double x = floor((log10(sqrt(1.0 + u2)) - lg_min) * nbins / (lg_max - lg_min));
+    int b = x < 0 ? 0 : (x > nbins - 1 ? nbins - 1 : (int)x);
+    out[b] += s->p[sp][5][p];
+  }
+  return 0;
+}
+
 /* ----------------------------------------------------------- diagnostics */
 int or_node_charge(void *st, double *q) {
   ost *s = (ost *)st;

@@ -92,6 +92,13 @@ typedef struct or_diag {
   double created;            /* weight of the pairs created (both species)   */
 } or_diag;
 
+/* Per-cell number density sum(w)/V and kinetic energy density
+ * sum(w m (gamma-1))/V of species sp (nr x nt, theta fastest; Sect. 5.2). */
+int or_species_maps(void *st, int sp, double *density, double *energy);
+/* Sum of weights of species sp in nbins bins uniform in log10(gamma) on
+ * [lg_min, lg_max), out-of-range particles in the end bins (Sect. 5.2). */
+int or_spectrum(void *st, int sp, int nbins, double lg_min, double lg_max, double *out);
+
 void *or_create(const or_config *cfg);
 double or_config_dt(const or_config *cfg);
 void or_destroy(void *st);

@@ -149,6 +149,7 @@ struct Offsets {
   size_t items;
   size_t qnode, rows, psi64;
   size_t ev[8];          // pair-creation events: key cell xo yo ur ut up w
+  size_t spec;           // spectrum bins (on request)
   int64_t ev_cap;
   int ntiles, ntt, max_items, nb, nparts;
   size_t total;
@@ -222,6 +223,7 @@ void layout(const hff_config &c, Offsets &o) {
   // pair-creation events of one step (bounded; overflow is latched)
   o.ev_cap = c.gamma_th > 0 ? cap / 4 + 1024 : 0;
   for (int k = 0; k < 8; ++k) o.ev[k] = o.ev_cap ? L.take((size_t)o.ev_cap * (k < 2 ? 4 : R)) : 0;
+  o.spec = L.take(4096 * 8);
   o.qnode = L.take(nn * 8);
   o.rows = L.take((nr + 1) * 8 * 8);
   o.psi64 = L.take(nn * 8);
@@ -1319,6 +1321,204 @@ int hff_status(hff_handle *h) {
 int hff_destroy(hff_handle *h) {
   if (!h) return fail(HFF_ERR_ARG, "null handle");
   destroy_handle(h);
+  return HFF_OK;
+}
+
+// ------------------------------------------------------------ maps, spectra
+int hff_species_maps(hff_handle *h, int inst, int species, double *density, double *energy) {
+  h = member(h, inst);
+  if (!h || species < 0 || species >= h->c.n_species) return fail(HFF_ERR_ARG, "bad arguments");
+  int rc = materialize_any(h);
+  if (rc != HFF_OK) return rc;
+  double *d = reinterpret_cast<double *>(h->base + h->o.qnode);   // both scratch areas hold nr x nt
+  double *e = reinterpret_cast<double *>(h->base + h->o.psi64);
+  const int par = h->c.sort_every > 0 ? h->parity : 0;
+  const double m = h->c.m[species];  // the FP64 mass of the configuration
+  if (h->c.precision == HFF_FP64) launch_maps<double>(h->pd[par], h->dg, species, m, d, e, h->st);
+  else launch_maps<float>(h->pf[par], h->dg, species, m, d, e, h->st);
+  CK(cudaGetLastError());
+  const size_t n = (size_t)h->c.nr * h->c.nt * sizeof(double);
+  if (density) CK(cudaMemcpyAsync(density, d, n, cudaMemcpyDeviceToHost, h->st));
+  if (energy) CK(cudaMemcpyAsync(energy, e, n, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+int hff_spectrum(hff_handle *h, int inst, int species, int nbins, double lg_min, double lg_max, double *out) {
+  h = member(h, inst);
+  if (!h || species < 0 || species >= h->c.n_species || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  if (nbins < 1 || nbins > 4096 || !(lg_max > lg_min)) return fail(HFF_ERR_ARG, "need 1 <= nbins <= 4096, lg_max > lg_min");
+  int rc = materialize_any(h);
+  if (rc != HFF_OK) return rc;
+  double *d = reinterpret_cast<double *>(h->base + h->o.spec);
+  const int par = h->c.sort_every > 0 ? h->parity : 0;
+  if (h->c.precision == HFF_FP64) launch_spectrum<double>(h->pd[par], species, nbins, lg_min, lg_max, d, h->st);
+  else launch_spectrum<float>(h->pf[par], species, nbins, lg_min, lg_max, d, h->st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, d, (size_t)nbins * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+// Blob: header, then E_r E_th E_ph dB_r dB_th dB_ph (instance precision), then
+// per species its live particles: cell (int32), xo yo ur ut up w.
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  hff_config cfg;
+  int64_t step;
+  int64_t count[kMaxSpecies];
+  double acc[5];
+  double rr;
+  uint64_t pushed[2];
+  uint64_t payload_bytes;
+};
+static const char kCkptMagic[8] = {'H', 'F', 'F', 'C', 'K', 'P', 'T', '1'};
+
+// configurations that describe the same run (capacity and the ramp scalar
+// may differ); field by field, so that struct padding never matters
+static bool same_run(const hff_config &a, const hff_config &b) {
+  bool eq = a.nr == b.nr && a.nt == b.nt && a.r_min == b.r_min && a.r_max == b.r_max && a.r_lc == b.r_lc &&
+            a.b_star == b.b_star && a.geom == b.geom && a.courant == b.courant && a.r_abs == b.r_abs &&
+            a.absorb_strength == b.absorb_strength && a.n_breaks == b.n_breaks && a.n_species == b.n_species &&
+            a.inject == b.inject && a.kappa_inj == b.kappa_inj && a.w_inj == b.w_inj && a.gamma_rad == b.gamma_rad &&
+            a.b_ref == b.b_ref && a.shell_r == b.shell_r && a.synth_psi_open == b.synth_psi_open &&
+            a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
+            a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s;
+  for (int k = 0; k < 4; ++k)
+    eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
+  return eq;
+}
+
+static size_t ckpt_payload(const hff_handle *h, const int64_t *count) {
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  size_t b = 0;
+  for (int k = 0; k < 6; ++k) b += (size_t)field_elems(h, k) * R;
+  for (int s = 0; s < h->c.n_species; ++s) b += (size_t)count[s] * (4 + 6 * R);
+  return b;
+}
+
+// Bring the instance to a sorted, gathered state (a sort of the particles
+// changes their order only) and read its counters.
+static int ckpt_settle(hff_handle *h, Small *sm) {
+  int rc = materialize_any(h);
+  if (rc == HFF_OK && h->c.sort_every > 0 && h->c.capacity > 0)
+    rc = h->c.precision == HFF_FP64 ? run_sort_now<double>(h, h->st) : run_sort_now<float>(h, h->st);
+  if (rc != HFF_OK) return rc;
+  CK(cudaMemcpyAsync(sm, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+int hff_checkpoint_size(hff_handle *h, int inst, size_t *bytes) {
+  h = member(h, inst);
+  if (!h || !bytes) return fail(HFF_ERR_ARG, "bad arguments");
+  Small sm;
+  const int rc = ckpt_settle(h, &sm);
+  if (rc != HFF_OK) return rc;
+  int64_t cnt[kMaxSpecies];
+  for (int s = 0; s < kMaxSpecies; ++s) cnt[s] = sm.count[s];
+  *bytes = sizeof(CkptHeader) + ckpt_payload(h, cnt);
+  return HFF_OK;
+}
+
+int hff_checkpoint_save(hff_handle *h, int inst, void *dst, size_t bytes) {
+  h = member(h, inst);
+  if (!h || !dst) return fail(HFF_ERR_ARG, "bad arguments");
+  Small sm;
+  int rc = ckpt_settle(h, &sm);
+  if (rc != HFF_OK) return rc;
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.header_bytes = sizeof(CkptHeader);
+  hd.cfg = h->c;
+  hd.step = h->step;
+  for (int s = 0; s < kMaxSpecies; ++s) hd.count[s] = sm.count[s];
+  for (int k = 0; k < 5; ++k) hd.acc[k] = sm.acc[k];
+  hd.rr = sm.rr;
+  hd.pushed[0] = sm.pushed[0];
+  hd.pushed[1] = sm.pushed[1];
+  hd.payload_bytes = ckpt_payload(h, hd.count);
+  if (bytes < sizeof(hd) + hd.payload_bytes) return fail(HFF_ERR_CAPACITY, "checkpoint buffer too small");
+  char *o = (char *)dst;
+  std::memcpy(o, &hd, sizeof(hd));
+  o += sizeof(hd);
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  for (int k = 0; k < 6; ++k) {
+    const size_t n = (size_t)field_elems(h, k) * R;
+    CK(cudaMemcpyAsync(o, h->base + h->o.f[k], n, cudaMemcpyDeviceToHost, h->st));
+    o += n;
+  }
+  const int pp = (h->c.sort_every > 0) ? h->parity : 0;
+  for (int s = 0; s < h->c.n_species; ++s)
+    for (int k = 0; k < 7; ++k) {
+      const size_t n = (size_t)hd.count[s] * (k == 0 ? 4 : R);
+      if (n) CK(cudaMemcpyAsync(o, h->base + h->o.part[pp][s][k], n, cudaMemcpyDeviceToHost, h->st));
+      o += n;
+    }
+  CK(cudaStreamSynchronize(h->st));
+  return HFF_OK;
+}
+
+int hff_checkpoint_load(hff_handle *h, int inst, const void *src, size_t bytes) {
+  h = member(h, inst);
+  if (!h || !src) return fail(HFF_ERR_ARG, "bad arguments");
+  if (bytes < sizeof(CkptHeader)) return fail(HFF_ERR_ARG, "not a checkpoint (too short)");
+  CkptHeader hd;
+  std::memcpy(&hd, src, sizeof(hd));
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(CkptHeader))
+    return fail(HFF_ERR_ARG, "not a checkpoint of this library version");
+  if (!same_run(hd.cfg, h->c))
+    return fail(HFF_ERR_ARG, "checkpoint of a different configuration (only capacity and rr_scale may differ)");
+  for (int s = 0; s < h->c.n_species; ++s)
+    if (hd.count[s] < 0 || hd.count[s] > h->c.capacity) return fail(HFF_ERR_CAPACITY, "checkpoint exceeds capacity");
+  if (hd.payload_bytes != ckpt_payload(h, hd.count) || bytes < sizeof(hd) + hd.payload_bytes)
+    return fail(HFF_ERR_ARG, "checkpoint truncated");
+  int rc = materialize_any(h);
+  if (rc != HFF_OK) return rc;
+  const char *in = (const char *)src + sizeof(hd);
+  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
+  for (int k = 0; k < 6; ++k) {
+    const size_t n = (size_t)field_elems(h, k) * R;
+    CK(cudaMemcpyAsync(h->base + h->o.f[k], in, n, cudaMemcpyHostToDevice, h->st));
+    in += n;
+  }
+  const int pp = (h->c.sort_every > 0) ? h->parity : 0;
+  for (int s = 0; s < h->c.n_species; ++s) {
+    for (int k = 0; k < 7; ++k) {
+      const size_t n = (size_t)hd.count[s] * (k == 0 ? 4 : R);
+      if (n) CK(cudaMemcpyAsync(h->base + h->o.part[pp][s][k], in, n, cudaMemcpyHostToDevice, h->st));
+      in += n;
+    }
+    if (h->c.capacity > hd.count[s])
+      CK(cudaMemsetAsync(h->base + h->o.part[pp][s][0] + hd.count[s] * 4, 0xFF,
+                         (size_t)(h->c.capacity - hd.count[s]) * 4, h->st));
+  }
+  // counters: the saved state was sorted, so the sorted prefix is everything
+  Small sm;
+  CK(cudaMemcpyAsync(&sm, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  for (int s = 0; s < kMaxSpecies; ++s) sm.count[s] = sm.count_sorted[s] = s < h->c.n_species ? hd.count[s] : 0;
+  sm.step = hd.step;
+  for (int k = 0; k < 5; ++k) sm.acc[k] = hd.acc[k];
+  sm.rr = hd.rr;
+  sm.pushed[0] = hd.pushed[0];
+  sm.pushed[1] = hd.pushed[1];
+  sm.status = 0;
+  sm.pe_count = 0;
+  CK(cudaMemcpyAsync(h->small, &sm, sizeof(Small), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->step = hd.step;
+  h->c.rr_scale = hd.rr;
+  // rebuild the tile bounds and the work list (the sort keeps the order)
+  if (h->c.sort_every > 0 && h->c.capacity > 0) {
+    rc = h->c.precision == HFF_FP64 ? run_sort_now<double>(h, h->st) : run_sort_now<float>(h, h->st);
+    if (rc != HFF_OK) return rc;
+  }
+  CK(cudaStreamSynchronize(h->st));
   return HFF_OK;
 }
 

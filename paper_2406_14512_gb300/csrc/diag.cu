@@ -151,6 +151,66 @@ __global__ void __launch_bounds__(256) k_diag_rows(Params<R> p, DiagGeom g, cons
   }
 }
 
+// Sect. 5.2 maps: sums of w and w m (gamma - 1) per cell, then divided by
+// the exact cell volume (2 pi / 3)(r_{i+1}^3 - r_i^3)(cos th_j - cos th_{j+1})
+template <typename R>
+__global__ void __launch_bounds__(256) k_species_sums(Params<R> p, int s, double m, double *dens, double *ener) {
+  const int64_t n = p.count[s];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int c = p.sp[s].cell[k];
+    if (c < 0) continue;
+    const double w = p.sp[s].w[k], u0 = p.sp[s].ur[k], u1 = p.sp[s].ut[k], u2 = p.sp[s].up[k];
+    const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+    atomicAdd(&dens[c], w);
+    atomicAdd(&ener[c], w * m * uu / (sqrt(1.0 + uu) + 1.0));  // gamma - 1 without cancellation
+  }
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_per_volume(Params<R> p, DiagGeom g, double *dens, double *ener) {
+  const int64_t n = (int64_t)p.nr * p.nt;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c / p.nt), j = (int)(c - (int64_t)i * p.nt);
+    const double a = g.rn[i], b = g.rn[i + 1];
+    const double v = 2.0 * kPi / 3.0 * (b * b * b - a * a * a) * g.dcp[j];
+    dens[c] /= v;
+    ener[c] /= v;
+  }
+}
+template <typename R>
+__global__ void __launch_bounds__(256) k_spectrum(Params<R> p, int s, int nbins, double lg0, double inv,
+                                                  double *out) {
+  extern __shared__ double hist[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0.0;
+  __syncthreads();
+  const int64_t n = p.count[s];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    if (p.sp[s].cell[k] < 0) continue;
+    const double u0 = p.sp[s].ur[k], u1 = p.sp[s].ut[k], u2 = p.sp[s].up[k];
+    const double lg = log10(sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2));
+    double x = floor((lg - lg0) * inv);
+    x = x < 0.0 ? 0.0 : (x > nbins - 1 ? (double)(nbins - 1) : x);
+    atomicAdd(&hist[(int)x], (double)p.sp[s].w[k]);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (hist[b] != 0.0) atomicAdd(&out[b], hist[b]);
+}
+
+template <typename R> void launch_maps(const Params<R> &p, const DiagGeom &g, int species, double mass,
+                                       double *dens, double *ener, cudaStream_t s) {
+  const size_t n = (size_t)p.nr * p.nt;
+  cudaMemsetAsync(dens, 0, n * sizeof(double), s);
+  cudaMemsetAsync(ener, 0, n * sizeof(double), s);
+  k_species_sums<R><<<1216, 256, 0, s>>>(p, species, mass, dens, ener);
+  k_per_volume<R><<<1216, 256, 0, s>>>(p, g, dens, ener);
+}
+template <typename R> void launch_spectrum(const Params<R> &p, int species, int nbins, double lg_min,
+                                           double lg_max, double *out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, (size_t)nbins * sizeof(double), s);
+  k_spectrum<R><<<608, 256, (size_t)nbins * sizeof(double), s>>>(p, species, nbins, lg_min,
+                                                                  nbins / (lg_max - lg_min), out);
+}
+
 template <typename R> void launch_psi64(const Params<R> &p, double *out, cudaStream_t s) {
   k_psi64<R><<<p.nr + 1, 256, 0, s>>>(p, out);
 }
@@ -162,6 +222,12 @@ template <typename R> void launch_diag(const Params<R> &p, const DiagGeom &g, do
   k_diag_rows<R><<<p.nr + 1, 256, 0, s>>>(p, g, q, rows);
 }
 
+template void launch_maps<float>(const Params<float> &, const DiagGeom &, int, double, double *, double *,
+                                 cudaStream_t);
+template void launch_maps<double>(const Params<double> &, const DiagGeom &, int, double, double *, double *,
+                                  cudaStream_t);
+template void launch_spectrum<float>(const Params<float> &, int, int, double, double, double *, cudaStream_t);
+template void launch_spectrum<double>(const Params<double> &, int, int, double, double, double *, cudaStream_t);
 template void launch_psi64<float>(const Params<float> &, double *, cudaStream_t);
 template void launch_psi64<double>(const Params<double> &, double *, cudaStream_t);
 template void launch_diag<float>(const Params<float> &, const DiagGeom &, double *, double *, double *,

@@ -14,5 +14,11 @@ struct DiagGeom {
 template <typename R> void launch_psi64(const Params<R> &p, double *out, cudaStream_t s);
 template <typename R> void launch_diag(const Params<R> &p, const DiagGeom &g, double *q, double *kin,
                                        double *cnt, double *rows, cudaStream_t s);
+// per-cell number and kinetic-energy densities of one species (nr x nt, FP64)
+template <typename R> void launch_maps(const Params<R> &p, const DiagGeom &g, int species, double mass,
+                                       double *dens, double *ener, cudaStream_t s);
+// weights of one species in nbins bins uniform in log10(gamma) (clamped ends)
+template <typename R> void launch_spectrum(const Params<R> &p, int species, int nbins, double lg_min,
+                                           double lg_max, double *out, cudaStream_t s);
 
 }  // namespace hff

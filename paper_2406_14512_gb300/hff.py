@@ -79,7 +79,8 @@ _lib = None
 SYMBOLS = ["hff_plan", "hff_init", "hff_load_particles", "hff_set_field", "hff_fields", "hff_step",
            "hff_step_timed", "hff_step_stages", "hff_set_scalar", "hff_particles", "hff_diagnostics", "hff_get_info",
            "hff_status", "hff_destroy", "hff_last_error", "hff_tile_order_noalloc",
-           "hff_noalloc_last_error"]
+           "hff_noalloc_last_error", "hff_species_maps", "hff_spectrum", "hff_checkpoint_size",
+           "hff_checkpoint_save", "hff_checkpoint_load"]
 NOALLOC_MAX_PARTICLES = 262144
 
 
@@ -110,6 +111,11 @@ def load(path: str = LIB_PATH):
         "hff_last_error": ([], C.c_char_p),
         "hff_tile_order_noalloc": ([vp, i64, i32, i32, i32, i32, vp, C.POINTER(i64), vp], C.c_int),
         "hff_noalloc_last_error": ([], C.c_char_p),
+        "hff_species_maps": ([vp, C.c_int, C.c_int, vp, vp], C.c_int),
+        "hff_spectrum": ([vp, C.c_int, C.c_int, C.c_int, d, d, vp], C.c_int),
+        "hff_checkpoint_size": ([vp, C.c_int, C.POINTER(sz)], C.c_int),
+        "hff_checkpoint_save": ([vp, C.c_int, vp, sz], C.c_int),
+        "hff_checkpoint_load": ([vp, C.c_int, vp, sz], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -247,6 +253,33 @@ def hff_last_error() -> str:
     return load().hff_last_error().decode()
 
 
+def hff_species_maps(h, inst, species, nr, nt):
+    d = np.empty((nr, nt), np.float64)
+    e = np.empty((nr, nt), np.float64)
+    _check(load().hff_species_maps(h, inst, species, d.ctypes.data_as(C.c_void_p), e.ctypes.data_as(C.c_void_p)))
+    return d, e
+
+
+def hff_spectrum(h, inst, species, nbins, lg_min, lg_max):
+    out = np.empty(nbins, np.float64)
+    _check(load().hff_spectrum(h, inst, species, nbins, lg_min, lg_max, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def hff_checkpoint_save(h, inst) -> np.ndarray:
+    """The checkpoint blob of instance inst as a uint8 array."""
+    n = C.c_size_t()
+    _check(load().hff_checkpoint_size(h, inst, C.byref(n)))
+    buf = np.empty(n.value, np.uint8)
+    _check(load().hff_checkpoint_save(h, inst, buf.ctypes.data_as(C.c_void_p), n.value))
+    return buf
+
+
+def hff_checkpoint_load(h, inst, blob) -> None:
+    b = np.ascontiguousarray(blob, np.uint8)
+    _check(load().hff_checkpoint_load(h, inst, b.ctypes.data_as(C.c_void_p), b.nbytes))
+
+
 def hff_tile_order_noalloc(cell_ptr: int, n: int, nr: int, nt: int, tile_r: int, tile_t: int,
                            order_ptr: int, stream: int) -> int:
     """Stable tile order of n device cell indices into order_ptr (device,
@@ -317,6 +350,26 @@ class _InstanceOps:
 
     def diagnostics(self):
         return hff_diagnostics(self.h, self.inst, self.nr)
+
+    def species_maps(self, species: int):
+        """(number density, kinetic energy density) per cell, FP64, nr x nt."""
+        return hff_species_maps(self.h, self.inst, species, self.nr, self.nt)
+
+    def spectrum(self, species: int, nbins: int, lg_min: float, lg_max: float) -> np.ndarray:
+        return hff_spectrum(self.h, self.inst, species, nbins, lg_min, lg_max)
+
+    def checkpoint(self) -> np.ndarray:
+        """Checkpoint blob (host bytes) of this instance."""
+        return hff_checkpoint_save(self.h, self.inst)
+
+    def restore(self, blob) -> None:
+        hff_checkpoint_load(self.h, self.inst, blob)
+
+    def save(self, path: str) -> None:
+        self.checkpoint().tofile(path)
+
+    def resume(self, path: str) -> None:
+        self.restore(np.fromfile(path, np.uint8))
 
 
 class _Stepping:
