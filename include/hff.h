@@ -129,6 +129,10 @@ typedef struct hff_config {
   double gamma_s;           /* Lorentz factor of each created particle (>= 1);
                                both move along the parent's direction, at its
                                position, with its weight; the parent is kept     */
+  int32_t inject_species[2];/* the two species the surface injection creates
+                               together: (0, 1) = e- and e+ (Sect. 4), (0, 2) =
+                               e- and protons extracted from the crust
+                               (Sect. 5.1); equal values mean (0, 1)             */
 } hff_config;
 
 typedef struct hff_info {

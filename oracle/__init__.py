@@ -42,7 +42,7 @@ class _Cfg(C.Structure):
         ("shell_r", C.c_double), ("synth_psi_open", C.c_double),
         ("seed", C.c_uint64), ("capacity", C.c_int64),
         ("tile_r", C.c_int32), ("tile_t", C.c_int32), ("sort_every", C.c_int32),
-        ("gamma_th", C.c_double), ("gamma_s", C.c_double),
+        ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
     ]
 
 
@@ -147,6 +147,8 @@ def _cfg_struct(cfg: dict) -> _Cfg:
     c.sort_every = int(cfg.get("sort_every", 0))
     c.gamma_th = float(cfg.get("gamma_th", 0.0))
     c.gamma_s = float(cfg.get("gamma_s", 0.0))
+    isp = list(cfg.get("inject_species", [0, 1]))
+    c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
     return c
 
 

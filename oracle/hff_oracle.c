@@ -841,6 +841,12 @@ static void ampere(ost *s) {
 static void inject(ost *s) {
   if (s->c.inject != OR_INJ_ON) return;
   int nt = s->nt, nsp = s->c.n_species < 2 ? s->c.n_species : 2;
+  /* e- with e+ (Sect. 4), or e- with protons from the crust (Sect. 5.1) */
+  int isp[2] = {0, 1};
+  if (s->c.inject_species[0] != s->c.inject_species[1]) {
+    isp[0] = s->c.inject_species[0];
+    isp[1] = s->c.inject_species[1];
+  }
   uint32_t key[2] = {(uint32_t)s->c.seed, (uint32_t)(s->c.seed >> 32)};
   for (int j = 0; j < nt; ++j) {
     int32_t need = s->target[j] - s->surf[j] / 2;
@@ -852,7 +858,8 @@ static void inject(ost *s) {
       double r = s->c.r_min * exp(ox * s->dlog), t = (j + oy) * s->dth;
       double v = s->omega * r * sin(t);
       double uphi = v / sqrt(1.0 - v * v);
-      for (int sp = 0; sp < nsp; ++sp) {
+      for (int ks = 0; ks < nsp; ++ks) {
+        int sp = isp[ks];
         if (s->n[sp] >= s->cap) { fprintf(stderr, "oracle: particle capacity exceeded\n"); abort(); }
         int64_t p = s->n[sp]++;
         s->cell[sp][p] = j; /* i = 0 */

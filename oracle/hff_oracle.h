@@ -78,6 +78,7 @@ typedef struct or_config {
   int32_t sort_every;        /* sort cadence in steps (0 = never)            */
   double gamma_th;           /* pair creation threshold (0 = off), Sect. 5.1 */
   double gamma_s;            /* Lorentz factor of the created pairs          */
+  int32_t inject_species[2]; /* species injected together; equal = (0, 1)   */
 } or_config;
 
 typedef struct or_diag {

@@ -121,6 +121,10 @@ int validate(const hff_config *c) {
   if (!(c->gamma_th == 0 || c->gamma_th > 1) || (c->gamma_th > 0 && !(c->gamma_s >= 1.0)))
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
+  if (c->inject_species[0] != c->inject_species[1])
+    for (int k = 0; k < 2; ++k)
+      if (c->inject_species[k] < 0 || c->inject_species[k] >= c->n_species)
+        return fail(HFF_ERR_ARG, "inject_species must name existing species");
   return HFF_OK;
 }
 
@@ -353,6 +357,10 @@ void fill_params(hff_handle *h) {
     p.seed_lo = (uint32_t)c.seed;
     p.seed_hi = (uint32_t)(c.seed >> 32);
     p.inject = c.inject;
+    p.n_inj = c.n_species < 2 ? c.n_species : 2;
+    const bool dflt = c.inject_species[0] == c.inject_species[1];
+    p.inj_sp[0] = dflt ? 0 : c.inject_species[0];
+    p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
     p.pushed = h->small->pushed;
@@ -1385,7 +1393,8 @@ static bool same_run(const hff_config &a, const hff_config &b) {
             a.inject == b.inject && a.kappa_inj == b.kappa_inj && a.w_inj == b.w_inj && a.gamma_rad == b.gamma_rad &&
             a.b_ref == b.b_ref && a.shell_r == b.shell_r && a.synth_psi_open == b.synth_psi_open &&
             a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
-            a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s;
+            a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s &&
+            a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1];
   for (int k = 0; k < 4; ++k)
     eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
   return eq;

@@ -117,6 +117,7 @@ struct Params {
   long long *step;          // device step counter (injection key)
   uint32_t seed_lo, seed_hi;
   int inject;
+  int n_inj, inj_sp[2];     // species created together by the injection
   R w_inj;
   double *acc;              // [4] injected, killed, radiated, nonfinite
   unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel

@@ -726,15 +726,15 @@ __global__ void __launch_bounds__(1024) k_inject_scan(Params<R> p) {
   if (threadIdx.x == 0) {
     const int total = s_carry;
     p.inj_prefix[nt] = total;
-    const int npair = p.n_species < 2 ? p.n_species : 2;
-    for (int s = 0; s < npair; ++s) {
+    for (int k = 0; k < p.n_inj; ++k) {
+      const int s = p.inj_sp[k];
       const long long base = p.count[s];
       p.inj_base[s] = base;
       long long end = base + total;
       if (end > p.cap) { end = p.cap; atomicOr(p.status, kStCapacity); }
       p.count[s] = end;
     }
-    atomicAdd(&p.acc[0], (double)total * (double)p.w_inj * npair);
+    atomicAdd(&p.acc[0], (double)total * (double)p.w_inj * p.n_inj);
   }
 }
 
@@ -745,7 +745,6 @@ __global__ void __launch_bounds__(128) k_inject_write(Params<R> p) {
   if (j < nt) {
     const int k0 = p.inj_prefix[j], n = p.inj_prefix[j + 1] - k0;
     const long long step = *p.step;
-    const int npair = p.n_species < 2 ? p.n_species : 2;
     for (int k = 0; k < n; ++k) {
       uint32_t c[4] = {(uint32_t)step, (uint32_t)((unsigned long long)step >> 32), (uint32_t)j, (uint32_t)k};
       philox4x32_10(c, p.seed_lo, p.seed_hi);
@@ -754,7 +753,8 @@ __global__ void __launch_bounds__(128) k_inject_write(Params<R> p) {
       const R r = p.t.rn[0] * exp(ox * p.dlog);
       const R v = p.omega * r * sin((R(j) + oy) * p.dth);
       const R uphi = v / sqrt(R(1) - v * v);
-      for (int s = 0; s < npair; ++s) {
+      for (int k2 = 0; k2 < p.n_inj; ++k2) {
+        const int s = p.inj_sp[k2];
         const long long q = p.inj_base[s] + k0 + k;
         if (q >= p.count[s]) continue;  // capacity reached (flagged by the scan)
         Species<R> S = p.sp[s];

@@ -46,7 +46,7 @@ class hff_config(C.Structure):
         ("shell_r", C.c_double), ("synth_psi_open", C.c_double), ("seed", C.c_uint64),
         ("capacity", C.c_int64), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
         ("sort_every", C.c_int32), ("precision", C.c_int32),
-        ("gamma_th", C.c_double), ("gamma_s", C.c_double),
+        ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
     ]
 
 
@@ -162,6 +162,8 @@ def config_struct(cfg: dict) -> hff_config:
     c.precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
     c.gamma_th = float(cfg.get("gamma_th", 0.0))
     c.gamma_s = float(cfg.get("gamma_s", 0.0))
+    isp = list(cfg.get("inject_species", [0, 1]))
+    c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
     return c
 
 

@@ -109,6 +109,14 @@ def config(name: str) -> dict:
             c.update(n_pairs=4000, steps=10, precision="fp32", place="uniform", momenta="powerlaw",
                      gamma_th=50.0, gamma_s=50.0 * 2.2e5 / 1e6)
             c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]
+        elif kind == "crust":    # e-, e+, protons: crust extraction of e- and p, pair creation (Sect. 5.1)
+            c = _base(72, 56, 30.0, 3.0, "synth", seed=17)
+            me = c["m"][0]
+            c.update(q=[-1.0, 1.0, 1.0], m=[me, me, 1836.0 * me], inject_species=[0, 2],
+                     psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=4000, steps=10,
+                     precision="fp32", place="band", sheet_frac=0.2, momenta="powerlaw",
+                     gamma_th=50.0, gamma_s=50.0 * 2.2e5 / 1e6)
+            c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / me
         elif kind == "michel":   # monopole, south hemisphere force-free (Sect. 4)
             c = _base(64, 64, 50.0 / 3.0, 5.0, "michel", seed=14)
             # sharp cut at the equator (Psi = Psi*), placed a hair below Psi* so

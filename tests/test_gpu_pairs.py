@@ -96,3 +96,37 @@ def test_ten_steps_with_pair_creation_and_sorting(env, precision):
     errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
     assert max(errs.values()) < tol, errs
     assert sim.status() == 0
+
+
+@pytest.mark.parametrize("precision,steps", [("fp32", 1), ("fp64", 10)])
+def test_crust_extraction_with_protons(env, precision, steps):
+    """Three species (e-, e+, protons with m_p = 1836 m_e), electrons and
+    protons injected from the surface (Sect. 5.1), pair creation and
+    radiation reaction on, Table 1 flux bands.  FP64 over ten steps with
+    sorting; FP32 over one step with the threshold margin checked."""
+    hff, workloads, oracle = env
+    cfg = workloads.config("small_crust")
+    cfg.update(precision=precision, sort_every=4, capacity=80000)
+    ps = workloads.particles(cfg, seed=25)
+    sim, ref = hff.Sim(cfg), oracle.Oracle(cfg)
+    for s in range(2):
+        sim.load(s, ps[s])
+        ref.set_particles(s, ps[s])
+    ref.sort_now()
+    sim.step(steps)
+    for _ in range(steps):
+        n = [ref.count(0), ref.count(1)]
+        ref.step(1)
+        if precision == "fp32":
+            assert margin_ok(ref, cfg, n)
+    d = ref.diagnostics()[0]
+    assert d.count[2] > 0
+    for s in range(3):
+        g, o = sim.particles(s), ref.particles(s)
+        bad, ties, err = particle_mismatches(g, o, cfg["nt"])
+        assert bad == 0 and ties <= max(2, len(o["cell"]) // 2000), (s, bad, ties)
+        assert err < 1e-5, err
+    tol = 1e-5 if precision == "fp32" else 1e-10
+    errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
+    assert max(errs.values()) < max(tol, 2e-4 if precision == "fp32" else tol), errs
+    assert sim.status() == 0

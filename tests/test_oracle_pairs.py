@@ -88,3 +88,46 @@ def test_gauss_law_with_pair_creation(oracle_mod):
         assert d.rho_max > 0
         assert d.gauss_max < 1e-9 * d.rho_max, (d.gauss_max, d.rho_max)
     assert d.created > 0
+
+
+def test_crust_extraction_injects_electrons_and_protons(oracle_mod):
+    """Sect. 5.1: the surface supplies electrons and protons (m_p = 1836 m_e)
+    in corotation with no poloidal momentum, topping up each eligible cell to
+    its target; with pair creation off the positron species gets nothing."""
+    cfg = workloads.config("small_crust")
+    cfg.update(precision="fp64", capacity=20000, sort_every=0, gamma_th=0.0)
+    o = oracle_mod.Oracle(cfg)
+    o.step(1, ST["inject"])
+    tgt = o.inject_targets()
+    assert tgt.sum() > 0
+    e, pos, pr = (o.particles(s) for s in range(3))
+    assert len(pos["cell"]) == 0
+    assert len(e["cell"]) == len(pr["cell"]) == tgt.sum()
+    for k in ("cell", "xo", "yo", "ur", "ut", "up", "w"):
+        assert np.array_equal(e[k], pr[k]), k           # co-located: neutral at birth
+    assert not e["ur"].any() and not e["ut"].any()
+    # corotation: u_phi = gamma v, v = Omega r sin(theta) at the particle
+    nt = cfg["nt"]
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / cfg["nr"]
+    r = cfg["r_min"] * np.exp(e["xo"] * d)
+    th = (e["cell"] % nt + e["yo"]) * math.pi / nt
+    v = r * np.sin(th) / cfg["r_lc"]
+    assert np.allclose(e["up"], v / np.sqrt(1 - v * v), rtol=1e-14, atol=0)
+    # per-cell counts equal the targets (first injection: no plasma yet)
+    assert np.array_equal(np.bincount(e["cell"], minlength=nt)[:nt], tgt)
+
+
+def test_crust_run_keeps_gauss_law_with_three_species(oracle_mod):
+    """e-, e+ and protons with injection, pair creation and radiation
+    reaction: Gauss's law to round-off in the PIC domain."""
+    cfg = workloads.config("small_crust")
+    cfg.update(precision="fp64", capacity=100000, sort_every=4, psi_break=[], f_break=[])
+    o = oracle_mod.Oracle(cfg)
+    ps = workloads.particles(cfg, seed=12)
+    for s in range(2):
+        o.set_particles(s, ps[s])
+    for _ in range(3):
+        o.step(4)
+        d, _ = o.diagnostics()
+        assert d.gauss_max < 1e-9 * d.rho_max, (d.gauss_max, d.rho_max)
+    assert d.count[2] > 0 and d.injected > 0
