@@ -133,6 +133,16 @@ typedef struct hff_config {
                                together: (0, 1) = e- and e+ (Sect. 4), (0, 2) =
                                e- and protons extracted from the crust
                                (Sect. 5.1); equal values mean (0, 1)             */
+  int32_t ff_delta_only;    /* what returns from the nodes to the staggered E
+                               after the renormalisation of Eqs. 25-26 (Sect. 3),
+                               by arithmetic means, weighted by f: 0 = the
+                               corrected field itself (E_r and E_th are then
+                               averaged 1-2-1 every step in the force-free
+                               domain; stable over long runs), 1 = only the
+                               corrections Delta E (second order on a stationary
+                               solution, but it lets a mode grow near the axis
+                               next to a force-free / PIC interface within
+                               ~1e4-1e5 steps on 1024^2 - 2048^2 grids)          */
 } hff_config;
 
 typedef struct hff_info {

@@ -43,6 +43,7 @@ class _Cfg(C.Structure):
         ("seed", C.c_uint64), ("capacity", C.c_int64),
         ("tile_r", C.c_int32), ("tile_t", C.c_int32), ("sort_every", C.c_int32),
         ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
+        ("ff_delta_only", C.c_int32),
     ]
 
 
@@ -149,6 +150,7 @@ def _cfg_struct(cfg: dict) -> _Cfg:
     c.gamma_s = float(cfg.get("gamma_s", 0.0))
     isp = list(cfg.get("inject_species", [0, 1]))
     c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
+    c.ff_delta_only = int(cfg.get("ff_delta_only", 0))
     return c
 
 

@@ -445,6 +445,15 @@ static void node_pass_b(ost *s) {
       double sc = (ep2 > b2) ? sqrt(b2 / ep2) : 1.0;
       for (int k = 0; k < 3; ++k) NODE(13 + k, i, j) = sc * ep[k] - e[k];
     }
+  /* reading "interpolate these back" literally: the corrected node field
+   * E'' = E + Delta E itself returns to the edges                         */
+  if (!s->c.ff_delta_only)
+    for (int i = 1; i < nr; ++i)
+      for (int j = 0; j <= nt; ++j) {
+        double e[3], b[3];
+        collocate(s, i, j, e, b);
+        for (int k = 0; k < 3; ++k) NODE(13 + k, i, j) += e[k];
+      }
 }
 
 /* Mean of a node quantity over the two nodes of a radial edge, using only
@@ -463,22 +472,27 @@ static double edge_r_mean(const ost *s, int k, int i, int j) {
  * Eqs. 29-31: full in the force-free domain, absent in pure PIC, linear
  * across the layer.  Psi on an edge is the mean of its nodes.               */
 static void correct_e(ost *s) {
-  int nr = s->nr, nt = s->nt;
+  int nr = s->nr, nt = s->nt, lit = s->c.ff_delta_only == 0;
   node_pass_b(s);
+  /* with the literal reading the edge value moves toward the mean of the
+   * corrected node fields, E <- E + f (<E''> - E); otherwise E += f <dE>   */
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j <= nt; ++j) {
       double f = blend(s, 0.5 * (PSI(i, j) + PSI(i + 1, j)));
-      if (f != 0.0) ER(i, j) += f * edge_r_mean(s, 13, i, j);
+      double m = edge_r_mean(s, 13, i, j);
+      if (f != 0.0) ER(i, j) += f * (lit ? m - ER(i, j) : m);
     }
   for (int i = 1; i < nr; ++i)
     for (int j = 0; j < nt; ++j) {
       double f = blend(s, 0.5 * (PSI(i, j) + PSI(i, j + 1)));
-      if (f != 0.0) ET(i, j) += f * 0.5 * (NODE(14, i, j) + NODE(14, i, j + 1));
+      double m = 0.5 * (NODE(14, i, j) + NODE(14, i, j + 1));
+      if (f != 0.0) ET(i, j) += f * (lit ? m - ET(i, j) : m);
     }
   for (int i = 1; i < nr; ++i)
     for (int j = 1; j < nt; ++j) {
       double f = blend(s, PSI(i, j));
-      if (f != 0.0) EP(i, j) += f * NODE(15, i, j);
+      double m = NODE(15, i, j);
+      if (f != 0.0) EP(i, j) += f * (lit ? m - EP(i, j) : m);
     }
 }
 

@@ -79,6 +79,8 @@ typedef struct or_config {
   double gamma_th;           /* pair creation threshold (0 = off), Sect. 5.1 */
   double gamma_s;            /* Lorentz factor of the created pairs          */
   int32_t inject_species[2]; /* species injected together; equal = (0, 1)   */
+  int32_t ff_delta_only;     /* 0: the corrected node E returns to the edges,
+                                1: only the corrections Delta E (Sect. 3)   */
 } or_config;
 
 typedef struct or_diag {

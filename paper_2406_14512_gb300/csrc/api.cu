@@ -361,6 +361,7 @@ void fill_params(hff_handle *h) {
     const bool dflt = c.inject_species[0] == c.inject_species[1];
     p.inj_sp[0] = dflt ? 0 : c.inject_species[0];
     p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
+    p.ff_interp_e = c.ff_delta_only ? 0 : 1;
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
     p.pushed = h->small->pushed;
@@ -1394,7 +1395,8 @@ static bool same_run(const hff_config &a, const hff_config &b) {
             a.b_ref == b.b_ref && a.shell_r == b.shell_r && a.synth_psi_open == b.synth_psi_open &&
             a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
             a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s &&
-            a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1];
+            a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1] &&
+            (a.ff_delta_only != 0) == (b.ff_delta_only != 0);
   for (int k = 0; k < 4; ++k)
     eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
   return eq;

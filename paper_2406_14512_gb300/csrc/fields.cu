@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
 // ----------------------------------------------------------- node pass B
 // Renormalisation at interior nodes from E^{n+1} and B^{n+1/2}:
 // E' = E - (E.B) B/B^2 (Eq. 25), E'' = sqrt(B^2/E'^2) E' if E'^2 > B^2 (Eq. 26).
+// Stores Delta E = E'' - E, or E'' itself when the corrected field returns to
+// the edges (ff_interp_e).
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
       d1 = sc * y - e[1];
       d2 = sc * z - e[2];
     }
+    if (p.ff_interp_e) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
   }
   p.f.der[ix(i, j, n1)] = d0;
   p.f.det[ix(i, j, n1)] = d1;
@@ -262,25 +265,39 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
 }
 
 // Delta E interpolated back to the staggered mesh by arithmetic means and
-// applied with the blend weight f (Sect. 3, Eqs. 29-31).
+// applied with the blend weight f (Sect. 3, Eqs. 29-31); or, with
+// ff_interp_e, the corrected node field itself: E <- E + f (<E''> - E).
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   const Fields<R> &f = p.f;
+  const bool lit = p.ff_interp_e != 0;
   if (i < nr) {
     const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
-    if (fb != R(0)) f.er[ix(i, j, n1)] += fb * edge_r_mean(f.der, i, j, nr, n1);
+    if (fb != R(0)) {
+      const int64_t k = ix(i, j, n1);
+      const R m = edge_r_mean(f.der, i, j, nr, n1);
+      f.er[k] += fb * (lit ? m - f.er[k] : m);
+    }
   }
   if (i >= 1 && i < nr) {
     if (j < nt) {
       const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
-      if (fb != R(0)) f.et[ix(i, j, nt)] += fb * R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]);
+      if (fb != R(0)) {
+        const int64_t k = ix(i, j, nt);
+        const R m = R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]);
+        f.et[k] += fb * (lit ? m - f.et[k] : m);
+      }
     }
     if (j >= 1 && j < nt) {
       const R fb = blend(p, f.psi[ix(i, j, n1)]);
-      if (fb != R(0)) f.ep[ix(i, j, n1)] += fb * f.dep[ix(i, j, n1)];
+      if (fb != R(0)) {
+        const int64_t k = ix(i, j, n1);
+        const R m = f.dep[k];
+        f.ep[k] += fb * (lit ? m - f.ep[k] : m);
+      }
     }
   }
 }

@@ -118,6 +118,7 @@ struct Params {
   uint32_t seed_lo, seed_hi;
   int inject;
   int n_inj, inj_sp[2];     // species created together by the injection
+  int ff_interp_e;          // 1: the corrected node E returns to the edges, 0: only Delta E
   R w_inj;
   double *acc;              // [4] injected, killed, radiated, nonfinite
   unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel

@@ -117,10 +117,11 @@ def test_vacuum_dipole_curl_free_second_order(oracle_mod):
     assert min(rates) > 1.8, (errs, rates)
 
 
-def michel_cfg(n, allff=True):
+def michel_cfg(n, allff=True, delta_only=0):
     c = mk(n, n, "michel", r_max=50.0 / 3.0, r_lc=5.0, r_abs=15.0)
     if allff:
         c.update(psi_break=[-1.0], f_break=[1.0])  # force-free everywhere
+    c["ff_delta_only"] = delta_only
     return c
 
 
@@ -159,12 +160,12 @@ def test_michel_perpendicular_current_second_order(oracle_mod):
     assert errs[-1] < 1e-2 and min(rates) > 1.7, (errs, rates)
 
 
-def test_michel_force_free_step_is_stationary(oracle_mod):
-    """One force-free step (which includes the renormalisation) leaves the
-    Michel monopole unchanged at O(h^2) per unit time (inside r_abs)."""
+def michel_step_change(oracle_mod, delta_only):
+    """max over fields of |one force-free step's change| / dt, r^2-weighted,
+    inside r_abs, at three resolutions."""
     errs = []
     for n in (32, 64, 128):
-        o = oracle_mod.Oracle(michel_cfg(n))
+        o = oracle_mod.Oracle(michel_cfg(n, delta_only=delta_only))
         before = o.fields()
         o.step(1, oracle_mod.ST["all"] & ~oracle_mod.ST["inject"] & ~oracle_mod.ST["sort"])
         after = o.fields()
@@ -175,15 +176,26 @@ def test_michel_force_free_step_is_stationary(oracle_mod):
             d = (after[k] - before[k])[1:iabs, 1:-1] / o.dt
             e = max(e, np.max(np.abs(d) * rn[1:iabs, None] ** 2))
         errs.append(e)
-    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    return errs, [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+
+
+def test_michel_force_free_step_is_stationary(oracle_mod):
+    """One force-free step (which includes the renormalisation) leaves the
+    Michel monopole unchanged: at O(h^2) per unit time when only the
+    corrections Delta E return to the edges; at O(h) per unit time (O(h^2)
+    per step) when the corrected E itself returns, since E_r and E_th are
+    then averaged 1-2-1 once per step."""
+    errs, rates = michel_step_change(oracle_mod, delta_only=1)
     assert min(rates) > 1.5, (errs, rates)
+    errs, rates = michel_step_change(oracle_mod, delta_only=0)
+    assert min(rates) > 0.9 and errs[-1] < 0.06, (errs, rates)
 
 
 def test_force_free_invariants_after_renormalisation(oracle_mod):
     """With uniform E and B every edge receives the same correction, so after
     Eqs. 25-26 the collocated fields satisfy E.B = 0 (Eq. 23) and
     E^2 <= B^2 at every interior node: a second renormalisation is void."""
-    c = mk(16, 14, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    c = mk(16, 14, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0], ff_delta_only=1)
     o = oracle_mod.Oracle(c)
     for k, v in zip(("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph"),
                     (1.1, -0.4, 2.0, 0.3, 0.9, -0.6)):
@@ -197,7 +209,7 @@ def test_force_free_invariants_after_renormalisation(oracle_mod):
 def test_node_renormalisation_closed_form(oracle_mod):
     """Eqs. 25-26 at one node with uniform collocated fields: E' is E minus
     its projection on B, then rescaled to |E'| = |B| if it exceeded it."""
-    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0], ff_delta_only=1)
     o = oracle_mod.Oracle(c)
     E = np.array([0.3, -1.7, 0.9])
     B = np.array([0.5, 0.2, -0.4])
@@ -249,3 +261,28 @@ def test_courant_matches_table1_ratio(oracle_mod):
     assert abs(dt_s - 4.3e-9) / 4.3e-9 < 0.02
     dr = 1e6 * (math.exp(math.log(50.0 / 3.0) / 8192) - 1.0)
     assert abs(dr - 3.4e2) / 3.4e2 < 0.02
+
+
+def test_corrected_field_returns_to_edges_closed_form(oracle_mod):
+    """Default reading of Sect. 3 ("interpolate these back"): the corrected
+    node field itself returns to the edges.  With uniform E and B every
+    interior edge becomes the renormalised field of Eqs. 25-26, and a second
+    pass leaves it unchanged."""
+    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    o = oracle_mod.Oracle(c)
+    E = np.array([0.3, -1.7, 0.9])
+    B = np.array([0.5, 0.2, -0.4])
+    for k, v in zip(("E_r", "E_th", "E_ph"), E):
+        o.set(k, np.full(o.shape(k), v))
+    for k, v in zip(("B_r", "B_th", "B_ph"), B):
+        o.set(k, np.full(o.shape(k), v))
+    o.step(1, oracle_mod.ST["correct"])
+    ep = E - E.dot(B) / B.dot(B) * B
+    if ep.dot(ep) > B.dot(B):
+        ep *= math.sqrt(B.dot(B) / ep.dot(ep))
+    got = np.array([o.get(k)[5, 6] for k in ("E_r", "E_th", "E_ph")])
+    assert np.allclose(got, ep, rtol=1e-13, atol=1e-14)
+    before = {k: o.get(k) for k in ("E_r", "E_th", "E_ph")}
+    o.step(1, oracle_mod.ST["correct"])
+    for k in before:
+        assert np.allclose(o.get(k)[3:-3, 3:-3], before[k][3:-3, 3:-3], rtol=1e-13, atol=1e-14), k
