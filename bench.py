@@ -263,6 +263,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--tile", default=None, help="tile_r x tile_t of the sort and the tiled push, e.g. 16x24")
+    ap.add_argument("--sort-every", type=int, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,6 +296,10 @@ def main():
         cfg["n_pairs"] = args.pairs
     if args.precision:
         cfg["precision"] = args.precision
+    if args.tile:
+        cfg["tile_r"], cfg["tile_t"] = (int(x) for x in args.tile.lower().split("x"))
+    if args.sort_every:
+        cfg["sort_every"] = args.sort_every
     cfg["seed"] = int(cfg["seed"]) + 1000 * rank
     cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
     prec = cfg.get("precision", "fp32")

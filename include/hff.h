@@ -121,7 +121,10 @@ typedef struct hff_config {
   uint64_t seed;            /* key of the injection generator                    */
   int64_t capacity;         /* particle slots per species                        */
   int32_t tile_r, tile_t;   /* sort tile in cells (0 = default 16 x 32)          */
-  int32_t sort_every;       /* sort cadence in steps, 1..8 (0 = never sort)      */
+  int32_t sort_every;       /* sort cadence in steps, 1..32 (0 = never sort); the
+                               push stages each tile with a halo of the farthest
+                               drift between sorts, so a long cadence needs small
+                               enough tiles (else HFF_ERR_ARG at init)           */
   int32_t precision;        /* HFF_FP32 or HFF_FP64                              */
   double gamma_th;          /* threshold pair creation (Sect. 5.1): a lepton whose
                                Lorentz factor exceeds gamma_th after its push

@@ -111,7 +111,7 @@ int validate(const hff_config *c) {
   for (int s = 0; s < c->n_species; ++s)
     if (!(c->m[s] > 0)) return fail(HFF_ERR_ARG, "masses must be positive");
   if (c->capacity < 0 || c->capacity > 2000000000LL) return fail(HFF_ERR_ARG, "capacity out of range");
-  if (c->sort_every < 0 || c->sort_every > 8) return fail(HFF_ERR_ARG, "sort_every must be 0..8");
+  if (c->sort_every < 0 || c->sort_every > 32) return fail(HFF_ERR_ARG, "sort_every must be 0..32");
   if (c->precision != HFF_FP32 && c->precision != HFF_FP64) return fail(HFF_ERR_ARG, "bad precision");
   const double dlog = std::log(c->r_max / c->r_min) / c->nr;
   const double xi_abs = std::log(c->r_abs / c->r_min) / dlog;

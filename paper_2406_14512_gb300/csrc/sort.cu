@@ -50,14 +50,9 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-  const int lane = threadIdx.x & 31;
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t e = base + r * kSortThreads + threadIdx.x;
-    // nearly sorted input puts most of a warp on one digit: one shared
-    // atomic per distinct digit of the warp
-    const uint32_t d = (e < a.n) ? ((load_key(a, e) >> a.shift) & 255u) : 256u;
-    const unsigned same = __match_any_sync(0xffffffffu, d);
-    if (d < 256u && lane == __ffs(same) - 1) atomicAdd(&h[d], (uint32_t)__popc(same));
+    if (e < a.n) atomicAdd(&h[(load_key(a, e) >> a.shift) & 255u], 1u);
   }
   __syncthreads();
   a.hist[(int64_t)threadIdx.x * a.nb + blockIdx.x] = h[threadIdx.x];
@@ -208,16 +203,38 @@ __global__ void __launch_bounds__(256) k_gather(Species<R> src, Species<R> dst, 
   }
 }
 
-// the count and the removed slots of a sort whose payload moves later
-__global__ void __launch_bounds__(256) k_finish(int32_t *dst_cell, const uint32_t *keys, uint32_t dead, int64_t n,
-                                                long long *count, long long *count_sorted, int species) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    if (keys[q] == dead) {
-      if (q == 0 || keys[q - 1] != dead) { count[species] = q; count_sorted[species] = q; }
-      dst_cell[q] = -1;
-      continue;
+// One pass over the sorted keys of a sort whose payload moves later: the
+// live count, cell = -1 in the removed slots of the destination, and the
+// tile bounds.  Four keys per thread (one 16-byte load; the keys buffer is
+// 256-byte aligned), plus the neighbours of the group.
+__global__ void __launch_bounds__(256) k_finish_bounds(int32_t *dst_cell, const uint32_t *keys, uint32_t dead,
+                                                       int64_t n, long long *count, long long *count_sorted,
+                                                       int species, int *start, int *end) {
+  const int64_t groups = (n + 3) / 4;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q0 = 4 * g;
+    uint32_t k[6];  // k[0] = key before the group, k[5] = key after it
+    if (q0 + 3 < n) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(keys + q0);
+      k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+    } else {
+      for (int e = 0; e < 4; ++e) k[1 + e] = (q0 + e < n) ? keys[q0 + e] : dead;
     }
-    if (q == n - 1) { count[species] = n; count_sorted[species] = n; }
+    k[0] = q0 > 0 ? keys[q0 - 1] : dead;
+    k[5] = q0 + 4 < n ? keys[q0 + 4] : dead;
+    for (int e = 0; e < 4; ++e) {
+      const int64_t q = q0 + e;
+      if (q >= n) break;
+      const uint32_t c = k[1 + e];
+      if (c == dead) {
+        if (q == 0 || k[e] != dead) { count[species] = q; count_sorted[species] = q; }
+        dst_cell[q] = -1;
+        continue;
+      }
+      if (q == n - 1) { count[species] = n; count_sorted[species] = n; }
+      if (q == 0 || k[e] != c) start[c] = (int)q;
+      if (q == n - 1 || k[2 + e] != c) end[c] = (int)(q + 1);
+    }
   }
 }
 
@@ -282,13 +299,6 @@ __global__ void __launch_bounds__(1024) k_worklist(const int *start, const int *
   if (threadIdx.x == 0) *n_items = (int)min((int)carry, max_items);
 }
 
-// blocks of 256 threads for one thread per element (the kernels keep a
-// grid-stride loop, so the cap only matters beyond 2^39 elements)
-static unsigned one_per_thread(int64_t n) {
-  const int64_t b = (n + 255) / 256;
-  return (unsigned)(b < 1 ? 1 : (b > 0x7fffffff ? 0x7fffffff : b));
-}
-
 static int bits_for(uint32_t v) {
   int b = 0;
   while ((1ull << b) <= v) ++b;
@@ -334,18 +344,20 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
   }
   // ki holds the sorted keys, p.sidx[s] the sorted order
   k_set_count<<<1, 1, 0, st>>>(p.count, p.count_sorted, s, (long long)n);
-  // one thread per slot: enough loads in flight to cover DRAM latency
-  const unsigned g1 = one_per_thread(n);
-  if (gather) k_gather<R><<<g1, 256, 0, st>>>(p.sp[s], dst, p.sidx[s], ki, dead, n, p.count, p.count_sorted, s);
-  else k_finish<<<g1, 256, 0, st>>>(dst.cell, ki, dead, n, p.count, p.count_sorted, s);
   cudaMemsetAsync(ss.tile_start, 0, sizeof(int) * (ss.ntiles + 1), st);
   cudaMemsetAsync(ss.tile_end, 0, sizeof(int) * (ss.ntiles + 1), st);
-  k_bounds<<<g1, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
+  if (gather) {
+    k_gather<R><<<1216, 256, 0, st>>>(p.sp[s], dst, p.sidx[s], ki, dead, n, p.count, p.count_sorted, s);
+    k_bounds<<<1216, 256, 0, st>>>(ki, n, dead, ss.tile_start, ss.tile_end);
+  } else {
+    k_finish_bounds<<<1216, 256, 0, st>>>(dst.cell, ki, dead, n, p.count, p.count_sorted, s, ss.tile_start,
+                                          ss.tile_end);
+  }
 }
 
 template <typename R>
 void launch_materialize(const Params<R> &p, int s, cudaStream_t st) {
-  k_gather_live<R><<<one_per_thread(p.cap), 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
+  k_gather_live<R><<<1216, 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
 }
 
 template <typename R>

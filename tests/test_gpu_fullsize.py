@@ -1,5 +1,5 @@
 """Parity at the full size of the benchmark workload (4096 x 4096 grid, 3e8
-e+-, FP32, tiles 16 x 32, sort every 8 steps), in the launch configuration
+e+-, FP32, tiles 16 x 24, sort every 12 steps), in the launch configuration
 that bench.py times.
 
 The oracle cannot push 3e8 particles in a test, so it is given every particle
