@@ -46,7 +46,7 @@ def test_plan_sizes_scale_with_grid_and_capacity(lib):
     assert 15e9 < b3 < 40e9, b3
 
 
-@pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=9), dict(n_breaks_bad=True),
+@pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=33), dict(n_breaks_bad=True),
                                  dict(r_abs=1e9), dict(precision_bad=True)])
 def test_invalid_configs_are_rejected(lib, bad):
     cfg = workloads.config("small_pic")
