@@ -169,7 +169,8 @@ def sample(name: str, n: int) -> dict:
     c = config(name)
     scale = (n * n) / float(c["nr"] * c["nt"])
     small = _base(n, n, c["r_max"], c["r_lc"], c["geom"], kappa=c["kappa_inj"], seed=c["seed"])
-    for k in ("psi_break", "f_break", "precision", "place", "sheet_frac", "momenta", "steps"):
+    for k in ("psi_break", "f_break", "precision", "place", "sheet_frac", "momenta", "steps", "tile_r", "tile_t",
+              "sort_every"):
         if k in c:
             small[k] = c[k]
     if c.get("gamma_rad", 0.0) > 0:
