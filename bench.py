@@ -157,17 +157,27 @@ def oracle_rate(name, n_grid, steps, warm=0):
     return pst / el, el, desc, cfg
 
 
+def describe(name, cfg):
+    """The workload named in `config` by both arms of the benchmark."""
+    return (f"{name}: {cfg['nr']}x{cfg['nt']} log-spherical grid, r in [1, {cfg['r_max']:g}] r*, "
+            f"R_LC = {cfg['r_lc']:g} r*, {2 * cfg['n_pairs']:.3g} e+-, Table 1 flux bands, "
+            f"synthetic dipole/split-monopole field")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     n_grid = 128
     rate, el, desc, cfg = oracle_rate(args.workload, n_grid, args.steps, warm=args.warmup)
+    from paper_2406_14512_gb300 import workloads
+    full = workloads.config(args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload} (sample {n_grid}x{n_grid})", "sample": desc},
+            "config": {"workload": describe(args.workload, full), "sample": desc,
+                       "note": "each step is the FP64 oracle on a bounded sample of this workload"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -446,9 +456,8 @@ def main():
         "dtype": "f32" if prec == "fp32" else "f64",
         "data": "synthetic",
         "config": {
-            "workload": f"{args.workload}: {cfg['nr']}x{cfg['nt']} log-spherical grid, r in [1, {cfg['r_max']:g}] r*, "
-                        f"R_LC = {cfg['r_lc']:g} r*, {2 * cfg['n_pairs']:.3g} e+- (live at start {n_live0}), "
-                        f"Table 1 flux bands, synthetic dipole/split-monopole field",
+            "workload": describe(args.workload, cfg),
+            "live_at_start": n_live0,
             "cell_steps_per_s": ws * cells * K / el,
             "particles_per_step": pst_all / K,
             "cells": cells,
