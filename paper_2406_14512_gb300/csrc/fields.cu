@@ -302,22 +302,6 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   }
 }
 
-// corotating star and zero tangential E at the outer wall and E_ph on the axis
-template <typename R>
-__global__ void k_bc(Params<R> p) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
-  if (j < nt) {
-    p.f.et[ix(0, j, nt)] = -p.omega * p.t.rn[0] * p.t.sh[j] * (p.f.br0[ix(0, j, nt)] + p.f.br[ix(0, j, nt)]);
-    p.f.et[ix(nr, j, nt)] = R(0);
-  }
-  if (j <= nt) { p.f.ep[ix(0, j, n1)] = R(0); p.f.ep[ix(nr, j, n1)] = R(0); }
-  for (int i = j; i <= nr; i += gridDim.x * blockDim.x) {
-    p.f.ep[ix(i, 0, n1)] = R(0);
-    p.f.ep[ix(i, nt, n1)] = R(0);
-  }
-}
-
 static inline dim3 row_grid(int rows, int nt) { return dim3((nt + 1 + kRowThreads - 1) / kRowThreads, rows); }
 
 template <typename R> size_t psi_smem(int nt) { return (size_t)(psi_pad(nt) + 2) * sizeof(R); }
@@ -340,10 +324,6 @@ template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s) {
   k_node_b<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
   k_correct<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
 }
-template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s) {
-  const int n = (p.nr > p.nt ? p.nr : p.nt) + 2;
-  k_bc<R><<<(n + 255) / 256, 256, 0, s>>>(p);
-}
 
 template <typename R>
 __global__ void k_combine(R *dst, const R *a, const R *b, int64_t n, R sign) {
@@ -364,8 +344,7 @@ template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
-  template void launch_correct<R>(const Params<R> &, cudaStream_t);            \
-  template void launch_bc<R>(const Params<R> &, cudaStream_t);
+  template void launch_correct<R>(const Params<R> &, cudaStream_t);
 HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST

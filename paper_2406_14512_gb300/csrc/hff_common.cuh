@@ -173,7 +173,6 @@ template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s);
 template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
-template <typename R> void launch_bc(const Params<R> &p, cudaStream_t s);
 // dst[k] = a[k] + sign * b[k], k < n (B <-> B - B_0 at the ABI)
 template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_t n, int sign, cudaStream_t s);
 
