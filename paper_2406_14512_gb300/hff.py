@@ -2,10 +2,20 @@
 
 Argument marshalling only: every step of the hybrid force-free / PIC update
 runs in the CUDA kernels of the library.  PyTorch supplies the device memory
-(one uint8 tensor per instance, sized by ``hff_plan``) and the CUDA stream.
-The functions keep the C names; :class:`Sim` is a small convenience owner of
-one instance.  There is no CPU fallback: if the library or a GPU is missing,
-the calls raise.
+(one uint8 tensor per instance or ensemble, sized by ``hff_plan``) and the
+CUDA stream.  The functions keep the C names; :class:`Sim` owns one instance,
+:class:`Ensemble` several independent ones stepped by one graph launch per
+step (``ens[k]`` is instance k).  Both give fields (``get``/``set``),
+particles (``load``, ``particles``, ``particle_views``), FP64 diagnostics,
+per-species density / energy maps and spectra, and checkpoints
+(``checkpoint``/``restore``, ``save``/``resume``).  There is no CPU fallback:
+if the library or a GPU is missing, the calls raise.
+
+    sim = Sim(workloads.config("c3"))
+    ps = workloads.particles(sim.cfg)
+    sim.load(0, ps[0]); sim.load(1, ps[1])
+    sim.step(100)
+    diag, L_of_r = sim.diagnostics()
 """
 from __future__ import annotations
 
