@@ -178,6 +178,10 @@ typedef struct hff_diag {
   double count[4];          /* live particles per species                        */
   double injected, killed, radiated, nonfinite; /* running totals (weights)      */
   double created;           /* weight of the created pairs (both species)        */
+  double clamps;            /* running count of E^2 > B^2 renormalisations
+                               (Eq. 26) at force-free nodes                      */
+  double nonfinite_fields;  /* non-finite E or B values now on the mesh; if any,
+                               HFF_ERR_NONFINITE is latched for hff_status       */
 } hff_diag;
 
 typedef struct hff_handle hff_handle;

@@ -50,7 +50,7 @@ typedef struct {
   int32_t *surf, *target;
   int64_t step;
   double rr_k[4];
-  double injected, killed, radiated, nonfinite, created;
+  double injected, killed, radiated, nonfinite, created, clamps;
   /* pair-creation events of the current step, in push order (species 0 by
    * particle index, then species 1): new cell, offsets, momentum, weight   */
   int64_t n_ev, cap_ev;
@@ -443,6 +443,7 @@ static void node_pass_b(ost *s) {
         ep2 += ep[k] * ep[k];
       }
       double sc = (ep2 > b2) ? sqrt(b2 / ep2) : 1.0;
+      if (ep2 > b2) s->clamps += 1; /* Eq. 26 applied at this node */
       for (int k = 0; k < 3; ++k) NODE(13 + k, i, j) = sc * ep[k] - e[k];
     }
   /* reading "interpolate these back" literally: the corrected node field
@@ -1088,5 +1089,12 @@ int or_diagnostics(void *st, or_diag *o, double *lprof) {
   o->radiated = s->radiated;
   o->nonfinite = s->nonfinite;
   o->created = s->created;
+  o->clamps = s->clamps;
+  {
+    double bad = 0;
+    for (int k = 0; k < 6; ++k)
+      for (int64_t q = 0; q < fsize(s, k); ++q) bad += !isfinite(s->f[k][q]);
+    o->nonfinite_fields = bad;
+  }
   return 0;
 }

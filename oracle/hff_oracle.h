@@ -93,6 +93,8 @@ typedef struct or_diag {
   double count[4];
   double injected, killed, radiated, nonfinite;
   double created;            /* weight of the pairs created (both species)   */
+  double clamps;             /* running count of E^2 > B^2 renormalisations  */
+  double nonfinite_fields;   /* non-finite E or B values on the mesh now     */
 } or_diag;
 
 /* Per-cell number density sum(w)/V and kinetic energy density

@@ -170,6 +170,7 @@ struct Small {  // device counters, one 256-byte block
   double kin[kMaxSpecies];
   double cnt[kMaxSpecies];
   unsigned long long pushed[2];
+  unsigned long long clamps;
   unsigned status;
   int n_items;
   int next;
@@ -366,6 +367,7 @@ void fill_params(hff_handle *h) {
     p.acc = h->small->acc;
     p.pushed = h->small->pushed;
     p.status = &h->small->status;
+    p.clamps = &h->small->clamps;
     p.tile_r = tile_r_of(c); p.tile_t = tile_t_of(c); p.ntt = o.ntt;
     p.pairs = c.gamma_th > 0 ? 1 : 0;
     p.gamma_th2 = (R)(c.gamma_th * c.gamma_th);
@@ -1227,7 +1229,7 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
   CK(cudaStreamSynchronize(h->st));
   std::memset(out, 0, sizeof(*out));
   out->psi_open = po;
-  double sin_ = 0, sout = 0, ue = 0, ub = 0, g2 = 0, gc = 0, gmax = 0, rmax = 0;
+  double sin_ = 0, sout = 0, ue = 0, ub = 0, g2 = 0, gc = 0, gmax = 0, rmax = 0, bad = 0;
   int nin = 0, nout = 0;
   for (int i = 0; i <= nr; ++i) {
     const double *o = &hr[(size_t)i * 8];
@@ -1238,6 +1240,7 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
       if (r >= 2 * h->c.r_lc && r <= 3 * h->c.r_lc) { sout += o[0]; nout++; }
     }
     ue += o[1]; ub += o[2]; gmax = std::fmax(gmax, o[3]); g2 += o[4]; gc += o[5]; rmax = std::fmax(rmax, o[6]);
+    bad += o[7];
   }
   out->l_in = nin ? sin_ / nin : 0;
   out->l_out = nout ? sout / nout : 0;
@@ -1253,6 +1256,13 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
   out->radiated = sm.acc[2];
   out->nonfinite = sm.acc[3];
   out->created = sm.acc[4];
+  out->clamps = (double)sm.clamps;
+  out->nonfinite_fields = bad;
+  if (bad > 0) {  // latched like the device-side errors, reported by hff_status
+    const unsigned bit = sm.status | kStNonfiniteField;
+    CK(cudaMemcpyAsync(&h->small->status, &bit, sizeof(bit), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   return HFF_OK;
 }
 
@@ -1324,6 +1334,7 @@ int hff_status(hff_handle *h) {
   if (st & kStCapacity) return fail(HFF_ERR_CAPACITY, "particle capacity exceeded on the device");
   if (st & kStWorklist) return fail(HFF_ERR_CAPACITY, "work list overflow");
   if (st & kStNonfinite) return fail(HFF_ERR_NONFINITE, "non-finite particle state removed");
+  if (st & kStNonfiniteField) return fail(HFF_ERR_NONFINITE, "non-finite field values (seen by hff_diagnostics)");
   return HFF_OK;
 }
 
@@ -1520,6 +1531,7 @@ int hff_checkpoint_load(hff_handle *h, int inst, const void *src, size_t bytes) 
   sm.pushed[1] = hd.pushed[1];
   sm.status = 0;
   sm.pe_count = 0;
+  sm.clamps = 0;
   CK(cudaMemcpyAsync(h->small, &sm, sizeof(Small), cudaMemcpyHostToDevice, h->st));
   CK(cudaStreamSynchronize(h->st));
   h->step = hd.step;

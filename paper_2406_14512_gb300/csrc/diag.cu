@@ -97,8 +97,15 @@ __global__ void __launch_bounds__(256) k_diag_rows(Params<R> p, DiagGeom g, cons
   auto Bt = [&](int64_t k) { return (double)f.bt0[k] + (double)f.bt[k]; };
   auto Bp = [&](int64_t k) { return (double)f.bp0[k] + (double)f.bp[k]; };
   auto Br = [&](int64_t k) { return (double)f.br0[k] + (double)f.br[k]; };
-  double L = 0, ue = 0, ub = 0, gmax = 0, g2 = 0, gcnt = 0, rmax = 0;
+  double L = 0, ue = 0, ub = 0, gmax = 0, g2 = 0, gcnt = 0, rmax = 0, bad = 0;
   for (int j = threadIdx.x; j <= nt; j += blockDim.x) {
+    // non-finite field values owned by (i, j) (failure detection)
+    if (i < nr) {
+      bad += !isfinite((double)f.er[ix(i, j, n1)]) + !isfinite((double)f.bt[ix(i, j, n1)]);
+      if (j < nt) bad += !isfinite((double)f.bp[ix(i, j, nt)]);
+    }
+    if (j < nt) bad += !isfinite((double)f.et[ix(i, j, nt)]) + !isfinite((double)f.br[ix(i, j, nt)]);
+    bad += !isfinite((double)f.ep[ix(i, j, n1)]);
     if (i < nr) {
       const double r = g.rh[i];
       if (j < nt) {
@@ -145,9 +152,10 @@ __global__ void __launch_bounds__(256) k_diag_rows(Params<R> p, DiagGeom g, cons
   gcnt = block_sum(gcnt, sh);
   gmax = block_max(gmax, sh);
   rmax = block_max(rmax, sh);
+  bad = block_sum(bad, sh);
   if (threadIdx.x == 0) {
     double *o = rows + (int64_t)i * 8;
-    o[0] = L / (4 * kPi); o[1] = ue; o[2] = ub; o[3] = gmax; o[4] = g2; o[5] = gcnt; o[6] = rmax; o[7] = 0;
+    o[0] = L / (4 * kPi); o[1] = ue; o[2] = ub; o[3] = gmax; o[4] = g2; o[5] = gcnt; o[6] = rmax; o[7] = bad;
   }
 }
 

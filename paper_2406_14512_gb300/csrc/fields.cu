@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   R d0 = 0, d1 = 0, d2 = 0;
+  bool clamped = false;
   if (i >= 1 && i < nr) {
     R e[3], b[3];
     collocate(p, i, j, e, b);
@@ -256,9 +257,14 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
       d0 = sc * x - e[0];
       d1 = sc * y - e[1];
       d2 = sc * z - e[2];
+      clamped = e2 > b2;
     }
     if (p.ff_interp_e) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
   }
+  // running count of Eq. 26 activations (failure detection: a force-free
+  // region that keeps needing the clamp is going unstable)
+  const unsigned act = __activemask(), m = __ballot_sync(act, clamped);
+  if (m && (threadIdx.x & 31) == (unsigned)(__ffs(act) - 1)) atomicAdd(p.clamps, (unsigned long long)__popc(m));
   p.f.der[ix(i, j, n1)] = d0;
   p.f.det[ix(i, j, n1)] = d1;
   p.f.dep[ix(i, j, n1)] = d2;

@@ -36,6 +36,7 @@ inline cudaError_t raise_smem_limit(size_t bytes) {
 constexpr unsigned kStCapacity = 1u;
 constexpr unsigned kStNonfinite = 2u;
 constexpr unsigned kStWorklist = 4u;
+constexpr unsigned kStNonfiniteField = 8u;
 
 template <typename R>
 struct Tables {
@@ -123,6 +124,7 @@ struct Params {
   double *acc;              // [4] injected, killed, radiated, nonfinite
   unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel
   unsigned *status;
+  unsigned long long *clamps;  // running count of E^2 > B^2 renormalisations (Eq. 26)
   int tile_r, tile_t, ntt;  // sort tiles
   // threshold pair creation (Sect. 5.1): events recorded by the push, the
   // pairs appended after the injection

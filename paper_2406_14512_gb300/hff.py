@@ -81,7 +81,7 @@ class hff_diag(C.Structure):
                 ("rho_max", C.c_double), ("u_e", C.c_double), ("u_b", C.c_double),
                 ("kinetic", C.c_double * 4), ("count", C.c_double * 4), ("injected", C.c_double),
                 ("killed", C.c_double), ("radiated", C.c_double), ("nonfinite", C.c_double),
-                ("created", C.c_double)]
+                ("created", C.c_double), ("clamps", C.c_double), ("nonfinite_fields", C.c_double)]
 
 
 _lib = None

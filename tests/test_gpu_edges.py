@@ -165,3 +165,38 @@ def test_deferred_gather_same_state(env):
                 np.testing.assert_allclose(parts[s][k], ref_p[s][k], rtol=1e-12, atol=1e-14)
         for f in fields:
             np.testing.assert_allclose(fields[f], ref_f[f], rtol=1e-11, atol=1e-14)
+
+
+def test_clamp_counter_matches_oracle(env):
+    """The running count of Eq. 26 activations equals the oracle's in FP64
+    over ten hybrid steps (same decisions at every node)."""
+    hff, workloads, oracle = env
+    cfg = workloads.config("small_hybrid")
+    cfg.update(capacity=40000, sort_every=4, precision="fp64")
+    ps = workloads.particles(cfg, n_pairs=4000, seed=43)
+    sim, ref = hff.Sim(cfg), oracle.Oracle(cfg)
+    for s in range(2):
+        sim.load(s, ps[s])
+        ref.set_particles(s, ps[s])
+    ref.sort_now()
+    sim.step(10)
+    ref.step(10)
+    g, o = sim.diagnostics()[0], ref.diagnostics()[0]
+    assert o.clamps > 0
+    assert g.clamps == o.clamps, (g.clamps, o.clamps)
+    assert g.nonfinite_fields == 0
+
+
+def test_nonfinite_field_is_detected_and_latched(env):
+    hff, workloads, _ = env
+    cfg = workloads.config("small_pic")
+    cfg.update(capacity=100, sort_every=0)
+    sim = hff.Sim(cfg)
+    er = sim.get("E_r")
+    er[5, 7] = np.nan
+    sim.set("E_r", er)
+    d, _ = sim.diagnostics()
+    assert d.nonfinite_fields >= 1
+    assert sim.status() == hff.HFF_ERR_NONFINITE
+    assert "field" in hff.hff_last_error()
+    assert sim.status() == 0

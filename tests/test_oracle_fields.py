@@ -286,3 +286,22 @@ def test_corrected_field_returns_to_edges_closed_form(oracle_mod):
     o.step(1, oracle_mod.ST["correct"])
     for k in before:
         assert np.allclose(o.get(k)[3:-3, 3:-3], before[k][3:-3, 3:-3], rtol=1e-13, atol=1e-14), k
+
+
+def test_failure_counters(oracle_mod):
+    """Failure detection: with uniform E perpendicular to B and |E| > |B|,
+    Eq. 26 clamps at every interior off-axis node once and never again (on
+    the axis the transverse E collocates to zero); a NaN planted in a field
+    is counted."""
+    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0])
+    o = oracle_mod.Oracle(c)
+    for k, v in zip(("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph"), (0.0, 2.0, 0.0, 1.0, 0.0, 0.0)):
+        o.set(k, np.full(o.shape(k), v))
+    o.step(1, oracle_mod.ST["correct"])
+    assert o.diagnostics()[0].clamps == (12 - 1) * (12 - 1)
+    o.step(1, oracle_mod.ST["correct"])
+    assert o.diagnostics()[0].clamps == (12 - 1) * (12 - 1)
+    er = o.get("E_r")
+    er[3, 4] = np.nan
+    o.set("E_r", er)
+    assert o.diagnostics()[0].nonfinite_fields == 1
