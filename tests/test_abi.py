@@ -69,3 +69,25 @@ def test_invalid_configs_are_rejected(lib, bad):
         hff.hff_plan(c)
     assert e.value.code == hff.HFF_ERR_ARG
     assert hff.hff_last_error()
+
+
+def test_header_is_plain_c_and_cxx(tmp_path):
+    """include/hff.h compiles as C99 and as C++17 on its own, and a C caller
+    can name every declared function (link-free: declarations only)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc") or not shutil.which("g++"):
+        pytest.skip("no host C compiler")
+    hdr = os.path.join(ROOT, "include", "hff.h")
+    for cc, lang, std in (("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")):
+        subprocess.run([cc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", "-x", lang, std, hdr], check=True)
+    src = tmp_path / "use.c"
+    src.write_text('#include "hff.h"\n'
+                   "int main(void) {\n"
+                   "  hff_config c = {0};\n  size_t b = 0;\n"
+                   "  void *f[] = {(void *)hff_plan, (void *)hff_init, (void *)hff_step, (void *)hff_fields,\n"
+                   "               (void *)hff_particles, (void *)hff_diagnostics, (void *)hff_checkpoint_save,\n"
+                   "               (void *)hff_spectrum, (void *)hff_tile_order_noalloc};\n"
+                   "  (void)f;\n  return hff_plan(&c, 1, &b) == 0 ? 1 : 0;\n}\n")
+    subprocess.run(["gcc", "-fsyntax-only", "-Wall", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src)],
+                   check=True)
