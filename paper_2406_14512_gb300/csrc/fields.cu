@@ -21,22 +21,59 @@ constexpr int kRowThreads = 128;
 
 // ------------------------------------------------------------ Psi (Eq. 27)
 // Psi(i, 0) = 0, Psi(i, j+1) = Psi(i, j) + B_r(i, j+1/2) r_i^2 dcp_j, an
-// inclusive prefix along theta accumulated in FP64.  One block per r row:
-// the row is staged through shared memory (coalesced in and out), each
-// thread sums a contiguous chunk serially in FP64 (one conversion and one
-// add per element), one block-wide scan of the chunk totals gives the
-// offsets, and the prefix is rounded to the working precision.  The staged
-// row is padded by one word every 32 (element j at j + j/32), so that the
-// threads of a warp, each walking its own contiguous chunk, hit distinct
+// inclusive prefix along theta.  One block per r row: the row is staged
+// through shared memory (coalesced in and out), each thread sums a
+// contiguous chunk serially, one block-wide scan of the chunk totals gives
+// the offsets, and the prefix is rounded to the working precision.  The
+// staged row is padded by one word every 32 (element j at j + j/32), so that
+// the threads of a warp, each walking its own contiguous chunk, hit distinct
 // banks.
+//
+// Accumulation: FP64 for FP64 instances.  For FP32 instances a compensated
+// pair of floats (Knuth's two-sum: the rounding error of every addition is
+// carried in a second float), about 44 significant bits, far below the FP32
+// rounding of the stored prefix and at FP32 instead of FP64 throughput.
 constexpr int kPsiThreads = 256;
 __host__ __device__ __forceinline__ int psi_pad(int j) { return j + (j >> 5); }
 
+struct Acc64 {
+  double v;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add(const Acc64 &o) { v += o.v; }
+  __device__ __forceinline__ Acc64 neg() const { return {-v}; }
+  __device__ __forceinline__ Acc64 shfl_up(int o) const { return {__shfl_up_sync(0xffffffffu, v, o)}; }
+  __device__ __forceinline__ double times(double r2) const { return r2 * v; }
+};
+struct Acc32x2 {
+  float hi, lo;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x, bv = s - hi;
+    lo += (hi - (s - bv)) + (x - bv);
+    hi = s;
+  }
+  __device__ __forceinline__ void add(const Acc32x2 &o) {
+    add(o.hi);
+    lo += o.lo;
+  }
+  __device__ __forceinline__ Acc32x2 neg() const { return {-hi, -lo}; }
+  __device__ __forceinline__ Acc32x2 shfl_up(int o) const {
+    return {__shfl_up_sync(0xffffffffu, hi, o), __shfl_up_sync(0xffffffffu, lo, o)};
+  }
+  // (hi + lo) * r2 with r2 split into two floats: one final rounding
+  __device__ __forceinline__ float times(double r2) const {
+    const float r2h = (float)r2, r2l = (float)(r2 - (double)r2h);
+    return fmaf(hi, r2h, fmaf(hi, r2l, lo * r2h));
+  }
+};
+template <typename R> struct PsiAccOf { using T = Acc64; };
+template <> struct PsiAccOf<float> { using T = Acc32x2; };
+
 template <typename R>
 __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
+  using A = typename PsiAccOf<R>::T;
   extern __shared__ __align__(16) unsigned char psmem[];
   R *row = reinterpret_cast<R *>(psmem);  // nt + 1 values
-  __shared__ double warp_tot[kPsiThreads / 32];
+  __shared__ A warp_tot[kPsiThreads / 32];
   const int i = blockIdx.x, nt = p.nt, tid = threadIdx.x;
   const R *br = p.f.br + (int64_t)i * nt;
   const R *br0 = p.f.br0 + (int64_t)i * nt;
@@ -44,27 +81,27 @@ __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   __syncthreads();
   const int chunk = (nt + kPsiThreads - 1) / kPsiThreads;
   const int j0 = min(tid * chunk, nt), j1 = min(j0 + chunk, nt);
-  double acc = 0.0;
-  for (int j = j0; j < j1; ++j) acc += (double)row[psi_pad(j)];
+  A acc{};
+  for (int j = j0; j < j1; ++j) acc.add(row[psi_pad(j)]);
   // exclusive scan of the chunk totals over the block
   const int lane = tid & 31, wid = tid >> 5;
-  double x = acc;
+  A x = acc;
   for (int o = 1; o < 32; o <<= 1) {
-    const double y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+    const A y = x.shfl_up(o);
+    if (lane >= o) x.add(y);
   }
   if (lane == 31) warp_tot[wid] = x;
   __syncthreads();
-  double off = x - acc;
-  for (int w = 0; w < wid; ++w) off += warp_tot[w];
+  A run = x;
+  run.add(acc.neg());
+  for (int w = 0; w < wid; ++w) run.add(warp_tot[w]);
   const double r2 = p.t.r2n[i];
   // rewrite the chunk in place with the prefix (inclusive, shifted by one)
-  double run = off;
   R prev = (j0 < j1) ? row[psi_pad(j0)] : R(0);
   for (int j = j0; j < j1; ++j) {
-    run += (double)prev;
+    run.add(prev);
     prev = (j + 1 < j1) ? row[psi_pad(j + 1)] : R(0);
-    row[psi_pad(j)] = (R)(r2 * run);  // becomes Psi(i, j+1)
+    row[psi_pad(j)] = (R)run.times(r2);  // becomes Psi(i, j+1)
   }
   __syncthreads();
   R *psi = p.f.psi + (int64_t)i * (nt + 1);
