@@ -523,13 +523,17 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
   if (K.creates) record_pair(p, K, q, i1 * nt + j1, xn, yn, uo, w);
 }
 
-// out-of-region fallback of the tiled kernel (kept out of line so that the
-// hot loop stays small)
+// out-of-region fallback of the tiled kernel.  It returns its counts by
+// value and takes the species index rather than the species constants:
+// arguments passed by reference to an out-of-line call would have to live
+// in local memory for the whole work item.
 template <typename R, bool kGather>
-__device__ __noinline__ void push_one_global(const Params<R> &p, const SpeciesConst<R> &K, int q, int qi, int i,
-                                             int j, Tally<R> &tl) {
+__device__ __forceinline__ Tally<R> push_one_global(const Params<R> &p, int s, int q, int qi, int i, int j) {
+  const SpeciesConst<R> K(p, s, kGather);
   GlobalMesh<R> g(p);
+  Tally<R> tl{R(0), R(0), 0u, 0u};
   push_one<R, kGather>(g, p, K, q, qi, i, j, tl);
+  return tl;
 }
 
 template <typename R>
@@ -575,7 +579,7 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
 // Region of a tile: cells [ti*TR - H, (ti+1)*TR + H) (and likewise in theta)
 // widened by the stencil: one node below, two above.
 template <typename R, bool kGather>
-__global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl, int halo) {
+__global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ Params<R> p, WorkList wl, int halo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
   R *base = reinterpret_cast<R *>(smem);
@@ -640,8 +644,11 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(Params<R> p, WorkList wl,
       decode_cell(p, c, i, j);
       if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
         push_one<R, kGather>(m, p, K, q, qi, i, j, tl);
-      else
-        push_one_global<R, kGather>(p, K, q, qi, i, j, tl);
+      else {
+        const Tally<R> t = push_one_global<R, kGather>(p, s, q, qi, i, j);
+        tl.killed += t.killed; tl.radiated += t.radiated;
+        tl.nonfinite += t.nonfinite; tl.pushed += t.pushed;
+      }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < area; k += blockDim.x) {
