@@ -87,3 +87,33 @@ def particle_mismatches(g, o, nt, tol_face=1e-5):
     if live.any():
         err = max(np.max(np.abs(g["xo"][live] - o["xo"][live])), np.max(np.abs(g["yo"][live] - o["yo"][live])))
     return bad, ties, float(err)
+
+
+def michel_fields(cfg, split=False, real=np.float64):
+    """Michel's monopole (Eqs. 32-35) on the staggered mesh from its closed
+    form: B_r = Psi*/r^2 (exact face average), B_ph = E_th =
+    -(Psi*/R_LC) sin(theta)/r at the points of each component, E_r = E_ph =
+    B_th = 0.  split=True reverses B and E in the southern hemisphere (the
+    split monopole, with its current sheet on the equator).  The southern
+    columns are mirrors of the northern ones (nt even), so that the two
+    hemispheres are exact negatives of each other when split."""
+    nr, nt = cfg["nr"], cfg["nt"]
+    assert nt % 2 == 0
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / nr
+    pst = cfg["b_star"] * cfg["r_min"] ** 2
+    rn = cfg["r_min"] * np.exp(np.arange(nr + 1) * d)
+    rh = cfg["r_min"] * np.exp((np.arange(nr) + 0.5) * d)
+    h = nt // 2
+    th = (np.arange(h) + 0.5) * math.pi / nt          # northern half columns
+    sgn = -1.0 if split else 1.0
+
+    def mirror(north, odd):
+        south = north[:, ::-1] * (sgn if odd else 1.0)
+        return np.concatenate([north, south], axis=1)
+
+    br = mirror(np.repeat((pst / rn ** 2)[:, None], h, axis=1), True)
+    bp = mirror(-(pst / cfg["r_lc"]) * np.sin(th)[None, :] / rh[:, None], True)
+    et = mirror(-(pst / cfg["r_lc"]) * np.sin(th)[None, :] / rn[:, None], True)
+    out = {"B_r": br, "B_ph": bp, "E_th": et,
+           "E_r": np.zeros((nr, nt + 1)), "E_ph": np.zeros((nr + 1, nt + 1)), "B_th": np.zeros((nr, nt + 1))}
+    return {k: v.astype(real) for k, v in out.items()}

@@ -10,6 +10,9 @@ by vector calculus (none of them re-types the oracle's own formulas):
   stationarity under one force-free step, the corotation boundary value,
   E.B = 0 and E^2 <= B^2 after the renormalisation of Eqs. 25-26, and the
   spin-down power L_M;
+* the split monopole (Michel's solution reversed in the south) away from its
+  equatorial sheet: the closed-form current, and one force-free step equal
+  to Michel's with the south reversed (the equations are odd in E and B);
 * the blending function of Eqs. 29-31 with the Table 1 bands.
 """
 import math
@@ -17,6 +20,7 @@ import math
 import numpy as np
 import pytest
 
+from helpers import michel_fields
 from paper_2406_14512_gb300 import workloads
 
 
@@ -158,6 +162,73 @@ def test_michel_perpendicular_current_second_order(oracle_mod):
         errs.append(max(e1.max(), e2.max()))
     rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert errs[-1] < 1e-2 and min(rates) > 1.7, (errs, rates)
+
+
+def set_fields(o, fields):
+    for k, v in fields.items():
+        o.set(k, v)
+
+
+def test_split_monopole_current_away_from_the_sheet(oracle_mod):
+    """Split monopole (Michel's solution with B and E reversed in the south):
+    more than 4 cells from the equatorial sheet the node current of Eq. 24
+    converges at second order to the closed form, which is Michel's with
+    rho and J_perp reversed in the south."""
+    errs = []
+    for n in (32, 64, 128):
+        cfg = michel_cfg(n)
+        o = oracle_mod.Oracle(cfg)
+        set_fields(o, michel_fields(cfg, split=True))
+        o.step(1, oracle_mod.ST["node"])
+        rn, _, tn, _ = grid(o)
+        r, t = rn[:, None], tn[None, :]
+        s = np.sign(np.cos(t))
+        om = 0.2
+        br, bp = s / r ** 2, -s * om * np.sin(t) / r
+        et = bp
+        rho = -s * om * np.cos(t) / (2 * math.pi * r ** 2)
+        b2 = br ** 2 + bp ** 2
+        jr = rho * et * bp / b2
+        jp = -rho * et * br / b2
+        far = np.abs(np.arange(n + 1) - n // 2) > 4
+        cols = far & (np.arange(n + 1) >= n // 8) & (np.arange(n + 1) <= n - n // 8)
+        sl_i = slice(n // 8, n // 2)
+        scale = np.abs(rho)[sl_i][:, cols].max()
+        e1 = np.abs(o.get("jperp_r") - jr)[sl_i][:, cols] / scale
+        e2 = np.abs(o.get("jperp_ph") - jp)[sl_i][:, cols] / scale
+        errs.append(max(e1.max(), e2.max()))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert errs[-1] < 1e-2 and min(rates) > 1.7, (errs, rates)
+
+
+def test_split_monopole_step_mirrors_michel(oracle_mod):
+    """The force-free equations are odd in (E, B), so one whole force-free
+    step of the split monopole must equal Michel's step with the southern
+    hemisphere reversed, exactly, wherever the stencils of one step (under two
+    cells) do not reach the sheet or the absorber; at the sheet, which is not
+    force-free, the two must differ."""
+    n = 64
+    cfg = michel_cfg(n)
+    after = {}
+    for split in (False, True):
+        o = oracle_mod.Oracle(cfg)
+        set_fields(o, michel_fields(cfg, split=split))
+        o.step(1, oracle_mod.ST["all"] & ~oracle_mod.ST["inject"] & ~oracle_mod.ST["sort"])
+        after[split] = o.fields()
+    rn, _, _, _ = grid(o)
+    rows = slice(0, int(np.searchsorted(rn, cfg["r_abs"])) - 8)
+    near_max = 0.0
+    for k in ("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph"):
+        a, b = after[True][k], after[False][k]
+        pos = np.arange(a.shape[1]) + (0.5 if a.shape[1] == n else 0.0)
+        dist = np.abs(pos - n / 2)
+        sgn = np.where(pos < n / 2, 1.0, -1.0)
+        scale = np.abs(b[rows]).max() + np.abs(a[rows]).max()
+        far = dist > 3
+        d = np.abs(a - sgn[None, :] * b)[rows]
+        assert d[:, far].max() <= 1e-14 * scale, (k, d[:, far].max(), scale)
+        near_max = max(near_max, d[:, dist <= 2].max() / scale)
+    assert near_max > 1e-3, near_max
 
 
 def michel_step_change(oracle_mod, delta_only):
