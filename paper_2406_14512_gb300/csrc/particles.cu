@@ -686,19 +686,35 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
     if constexpr (kFixed) {
       // bounds of the fixed-point deposit: the largest |w| of the item and
       // the largest count of its particles in one cell of the region
+      // (four particles per thread and round, so that eight loads are in
+      // flight: this loop has almost no arithmetic to hide them behind)
       float wmx = 0.f;
       bool bad = false;
-      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const int qi = kGather ? (int)K.sidx[q] : q;
-        const int c = K.In.cell[qi];
-        if (c < 0) continue;
-        const float w = fabsf((float)K.In.w[qi]);
-        bad |= !(w <= 3.0e38f);
-        wmx = fmaxf(wmx, w);
-        int i, j;
-        decode_cell(p, c, i, j);
-        if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-          atomicAdd(&m.s_hist[m.o(i, j)], 1);
+      for (int q = q0 + threadIdx.x; q < q1; q += 4 * blockDim.x) {
+        int c[4];
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qq = q + u * (int)blockDim.x;
+          c[u] = -1;
+          w[u] = 0.f;
+          if (qq < q1) {
+            const int qi = kGather ? (int)K.sidx[qq] : qq;
+            c[u] = K.In.cell[qi];
+            w[u] = (float)K.In.w[qi];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (c[u] < 0) continue;
+          const float aw = fabsf(w[u]);
+          bad |= !(aw <= 3.0e38f);
+          wmx = fmaxf(wmx, aw);
+          int i, j;
+          decode_cell(p, c[u], i, j);
+          if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
+            atomicAdd(&m.s_hist[m.o(i, j)], 1);
+        }
       }
       for (int o = 16; o > 0; o >>= 1) wmx = fmaxf(wmx, __shfl_xor_sync(0xffffffffu, wmx, o));
       if ((threadIdx.x & 31) == 0) atomicMax(&s_wmax, __float_as_uint(wmx));
