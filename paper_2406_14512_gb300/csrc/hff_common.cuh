@@ -15,7 +15,6 @@ constexpr int kMaxSpecies = 4;
 constexpr int kMaxBreaks = 4;
 constexpr double kPi = 3.14159265358979323846;
 
-// status bits latched on the device
 // Raises (never lowers) the dynamic shared-memory limit of a kernel on the
 // current device.  The limit is a property of the kernel, shared by every
 // instance in the process, so instances with different tile sizes can live
@@ -33,6 +32,7 @@ inline cudaError_t raise_smem_limit(size_t bytes) {
   return e;
 }
 
+// status bits latched on the device
 constexpr unsigned kStCapacity = 1u;
 constexpr unsigned kStNonfinite = 2u;
 constexpr unsigned kStWorklist = 4u;
