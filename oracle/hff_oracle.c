@@ -27,7 +27,9 @@
  *   8. sort        : stable sort by tile key with compaction, every k steps
  *
  * Parity pins for each part live in tests/test_oracle_*.py.  Parity unpinned:
- * the absorber profile (the paper only cites an earlier work for it).
+ * the exact absorber profile (the paper only cites an earlier work for it);
+ * its purpose is pinned (an outgoing pulse passes r_abs undamped, decays
+ * monotonically in the layer and is not sent back).
  */
 #include "hff_oracle.h"
 
