@@ -125,12 +125,7 @@ typedef struct hff_config {
                                push stages each tile with a halo of the farthest
                                drift between sorts, so a long cadence needs small
                                enough tiles (else HFF_ERR_ARG at init)           */
-  int32_t precision;        /* HFF_FP32 or HFF_FP64.  In FP32 the tiled push
-                               sums each tile's currents as fixed-point integers
-                               (power-of-two scales bounded by the largest |q w|,
-                               the Courant displacement and the densest cell) and
-                               adds the sums to the mesh in FP32; FP64 sums in
-                               FP64                                              */
+  int32_t precision;        /* HFF_FP32 or HFF_FP64                              */
   double gamma_th;          /* threshold pair creation (Sect. 5.1): a lepton whose
                                Lorentz factor exceeds gamma_th after its push
                                creates an e+- pair (0 = off, else > 1)           */

@@ -11,8 +11,7 @@
 //    sorts) into shared memory, accumulates J in shared memory with shared
 //    atomics, and flushes the tile's J with one global atomic per nonzero
 //    entry.  Particles of a tile are contiguous, so the particle stream is
-//    read and written once, fully coalesced.  In FP32 the shared J is a
-//    fixed-point integer sum (see FixedPoint below).
+//    read and written once, fully coalesced.
 //  * k_push_tail -- particles appended since the last sort (injection) and
 //    the no-sort configuration: gathers through L1/L2 and global atomics.
 #include <type_traits>
@@ -64,9 +63,7 @@ struct SharedMesh {
   R *s_er, *s_et, *s_ep, *s_br, *s_bt, *s_bp, *s_jr, *s_jt, *s_jp;
   R *s_rn, *s_sn, *s_cn;   // row / column tables of the region
   uint8_t *s_ff;
-  int *s_hist;             // particles per cell of the region (FP32 work items)
   int i0, j0, lt;
-  R fxr, fxt, fxp;         // fixed-point scales of the shared J_r, J_th, J_ph (FP32)
   __device__ __forceinline__ int o(int i, int j) const { return (i - i0) * lt + (j - j0); }
   __device__ __forceinline__ R er(int i, int j) const { return s_er[o(i, j)]; }
   __device__ __forceinline__ R et(int i, int j) const { return s_et[o(i, j)]; }
@@ -328,46 +325,6 @@ __device__ __forceinline__ Axis<R> axis_weights(R x0, R X1) {
   return w;
 }
 
-// FixedPoint: in FP32 work items the shared J accumulates integers
-// round(v S) with native 32-bit shared atomics (FP32 shared atomic adds run
-// as compare-and-swap loops) and the flush returns sum / S.  Each component
-// has its own power-of-two scale per work item, so the scaling is exact, and
-// each scale obeys two bounds.  Every contribution has |v| <= W = |q| max w
-// times a component factor: for J_r and J_th the charge crossing one face,
-// at most the displacement in cells (the cumulative linear weight is
-// 1-Lipschitz), which the speed of light bounds by -ln(1 - dt/r)/D and
-// asin(dt/r)/dtheta at the innermost radius r of the region (axis
-// reflection and the stop at the star only shorten it), capped at 1; for
-// J_ph, |v_phi| < c = 1.  And a node receives at most one contribution per
-// particle whose start cell lies in the 4 x 4 cells around it, at most
-// 16 cmax with cmax the largest particle count of one cell.  So
-// 16 cmax B S <= 2^30 (B the bound of |v|) keeps every sum inside int32 with
-// a factor 2 to spare, and B S <= 2^21 keeps v S inside the range where
-// adding 1.5 x 2^23 rounds it to an integer in the low mantissa bits (round
-// to nearest even).  The integer sums do not depend on the order of the
-// atomics.
-__device__ __forceinline__ int floor_log2(float x) {  // x > 0, finite
-  int e;
-  frexpf(x, &e);
-  return e - 1;
-}
-__device__ __forceinline__ float fixed_scale(float w, int cmax) {
-  if (!(w > 0.f) || cmax <= 0) return 1.f;
-  const int e1 = floor_log2(1073741824.f / (16.f * (float)cmax * w));
-  const int e2 = floor_log2(2097152.f / w);
-  return ldexpf(1.f, min(e1, e2));
-}
-__device__ __forceinline__ void dep_add(float *a, float v, float s) {
-  atomicAdd(reinterpret_cast<int *>(a), __float_as_int(fmaf(v, s, 12582912.f)) - 0x4B400000);
-}
-__device__ __forceinline__ void dep_add(double *a, double v, double) {
-  if (v != 0.0) atomicAdd(a, v);
-}
-__device__ __forceinline__ bool dep_nonzero(float v) { return __float_as_int(v) != 0; }
-__device__ __forceinline__ bool dep_nonzero(double v) { return v != 0.0; }
-__device__ __forceinline__ float dep_value(float v, float s) { return (float)__float_as_int(v) * (1.f / s); }
-__device__ __forceinline__ double dep_value(double v, double) { return v; }
-
 template <typename R>
 __device__ __forceinline__ void deposit_sh(const SharedMesh<R> &m, R qw, int i0, int j0, R x0, R y0, R X1, R Y1,
                                            R vphi) {
@@ -380,14 +337,14 @@ __device__ __forceinline__ void deposit_sh(const SharedMesh<R> &m, R qw, int i0,
     const R v[6] = {g0 * ay.m0, g0 * ay.m1, g0 * ay.m2, g1 * ay.m0, g1 * ay.m1, g1 * ay.m2};
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      dep_add(&m.s_jr[ob + (k / 3) * lt + k % 3], v[k], m.fxr);
+      if (v[k] != R(0)) atomicAdd(&m.s_jr[ob + (k / 3) * lt + k % 3], v[k]);
   }
   {
     const R g0 = nq * ay.f0, g1 = nq * ay.f1;
     const R v[6] = {g0 * ax.m0, g0 * ax.m1, g0 * ax.m2, g1 * ax.m0, g1 * ax.m1, g1 * ax.m2};
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      dep_add(&m.s_jt[ob + (k % 3) * lt + k / 3], v[k], m.fxt);
+      if (v[k] != R(0)) atomicAdd(&m.s_jt[ob + (k % 3) * lt + k / 3], v[k]);
   }
   {
     const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
@@ -400,7 +357,7 @@ __device__ __forceinline__ void deposit_sh(const SharedMesh<R> &m, R qw, int i0,
     const int op = m.o(i0 + km, j0 + lm);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      dep_add(&m.s_jp[op + (k / 2) * lt + k % 2], v[k], m.fxp);
+      if (v[k] != R(0)) atomicAdd(&m.s_jp[op + (k / 2) * lt + k % 2], v[k]);
   }
 }
 
@@ -627,25 +584,17 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
   const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
   R *base = reinterpret_cast<R *>(smem);
   SharedMesh<R> m;
-  m.fxr = m.fxt = m.fxp = R(1);
   m.s_er = base; m.s_et = base + area; m.s_ep = base + 2 * area;
   m.s_br = base + 3 * area; m.s_bt = base + 4 * area; m.s_bp = base + 5 * area;
   m.s_jr = base + 6 * area; m.s_jt = base + 7 * area; m.s_jp = base + 8 * area;
   m.s_rn = base + 9 * area; m.s_sn = m.s_rn + lr; m.s_cn = m.s_sn + lt;
-  m.s_hist = reinterpret_cast<int *>(m.s_cn + lt);
-  m.s_ff = reinterpret_cast<uint8_t *>(m.s_hist + area);
+  m.s_ff = reinterpret_cast<uint8_t *>(m.s_cn + lt);
   m.lt = lt;
-  constexpr bool kFixed = std::is_same<R, float>::value;
-  __shared__ int s_item, s_cmax;
-  __shared__ unsigned s_wmax;
+  __shared__ int s_item;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   Tally<R> tl{R(0), R(0), 0u, 0u};
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_item = atomicAdd(wl.next, 1);
-      s_cmax = 0;
-      s_wmax = 0u;
-    }
+    if (threadIdx.x == 0) s_item = atomicAdd(wl.next, 1);
     __syncthreads();
     const int it = s_item;
     if (it >= *wl.n_items) break;
@@ -669,7 +618,6 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
       m.s_bp[k] = p.f.bp0[kp] + p.f.bp[kp];
       m.s_ff[k] = (gi >= 0 && gj >= 0 && gi < nr && gj < nt) ? p.f.ffcell[ix(gi, gj, nt)] : 1;
       m.s_jr[k] = R(0); m.s_jt[k] = R(0); m.s_jp[k] = R(0);
-      m.s_hist[k] = 0;
     }
     for (int k = threadIdx.x; k < lr; k += blockDim.x) {
       const int gi = m.i0 + k;
@@ -683,56 +631,6 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
     const SpeciesConst<R> K(p, s, kGather);
     __syncthreads();
     const int q0 = item.z, q1 = item.z + item.w;
-    if constexpr (kFixed) {
-      // bounds of the fixed-point deposit: the largest |w| of the item and
-      // the largest count of its particles in one cell of the region
-      // (four particles per thread and round, so that eight loads are in
-      // flight: this loop has almost no arithmetic to hide them behind)
-      float wmx = 0.f;
-      bool bad = false;
-      for (int q = q0 + threadIdx.x; q < q1; q += 4 * blockDim.x) {
-        int c[4];
-        float w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int qq = q + u * (int)blockDim.x;
-          c[u] = -1;
-          w[u] = 0.f;
-          if (qq < q1) {
-            const int qi = kGather ? (int)K.sidx[qq] : qq;
-            c[u] = K.In.cell[qi];
-            w[u] = (float)K.In.w[qi];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (c[u] < 0) continue;
-          const float aw = fabsf(w[u]);
-          bad |= !(aw <= 3.0e38f);
-          wmx = fmaxf(wmx, aw);
-          int i, j;
-          decode_cell(p, c[u], i, j);
-          if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-            atomicAdd(&m.s_hist[m.o(i, j)], 1);
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) wmx = fmaxf(wmx, __shfl_xor_sync(0xffffffffu, wmx, o));
-      if ((threadIdx.x & 31) == 0) atomicMax(&s_wmax, __float_as_uint(wmx));
-      if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.status, kStNonfinite);
-      __syncthreads();
-      int cm = 0;
-      for (int k = threadIdx.x; k < area; k += blockDim.x) cm = max(cm, m.s_hist[k]);
-      for (int o = 16; o > 0; o >>= 1) cm = max(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-      if ((threadIdx.x & 31) == 0) atomicMax(&s_cmax, cm);
-      __syncthreads();
-      const float wq = __uint_as_float(s_wmax) * fabsf((float)K.q);
-      const float ri = (float)p.t.rn[max(m.i0, 0)], a = fminf((float)p.dt / ri, 1.f);
-      const float fr = fminf(1.f, -log1pf(-fminf(a, 0.999f)) * (float)p.inv_dlog);
-      const float ft = fminf(1.f, asinf(a) * (float)p.inv_dth);
-      m.fxr = fixed_scale(wq * fr, s_cmax);
-      m.fxt = fixed_scale(wq * ft, s_cmax);
-      m.fxp = fixed_scale(wq, s_cmax);
-    }
     // a particle is handled in shared memory when its whole stencil (start
     // cell -1 .. +2 in both directions) lies inside the region
     for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
@@ -758,12 +656,12 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
       const int gi = m.i0 + a, gj = m.j0 + c;
       if (gi < 0 || gj < 0) continue;
       // raw fluxes -> current densities (face areas, node volumes, dt)
-      if (dep_nonzero(m.s_jr[k]) && gi < nr && gj <= nt)
-        atomicAdd(&p.f.jr[ix(gi, gj, n1)], dep_value(m.s_jr[k], m.fxr) * p.t.dep_r[gi] * p.t.inv_dch[gj]);
-      if (dep_nonzero(m.s_jt[k]) && gi <= nr && gj < nt)
-        atomicAdd(&p.f.jt[ix(gi, gj, nt)], dep_value(m.s_jt[k], m.fxt) * p.t.dep_t[gi] * p.t.inv_sh[gj]);
-      if (dep_nonzero(m.s_jp[k]) && gi <= nr && gj <= nt)
-        atomicAdd(&p.f.jp[ix(gi, gj, n1)], dep_value(m.s_jp[k], m.fxp) * p.t.dep_p[gi] * p.t.inv_dch[gj]);
+      if (m.s_jr[k] != R(0) && gi < nr && gj <= nt)
+        atomicAdd(&p.f.jr[ix(gi, gj, n1)], m.s_jr[k] * p.t.dep_r[gi] * p.t.inv_dch[gj]);
+      if (m.s_jt[k] != R(0) && gi <= nr && gj < nt)
+        atomicAdd(&p.f.jt[ix(gi, gj, nt)], m.s_jt[k] * p.t.dep_t[gi] * p.t.inv_sh[gj]);
+      if (m.s_jp[k] != R(0) && gi <= nr && gj <= nt)
+        atomicAdd(&p.f.jp[ix(gi, gj, n1)], m.s_jp[k] * p.t.dep_p[gi] * p.t.inv_dch[gj]);
     }
     __syncthreads();
   }
@@ -772,7 +670,7 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
 
 template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo) {
   const size_t lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
-  return area * (9 * sizeof(R) + sizeof(int) + 1) + (lr + 2 * lt) * sizeof(R);
+  return area * (9 * sizeof(R) + 1) + (lr + 2 * lt) * sizeof(R);
 }
 
 template <typename R> void launch_push_tail(const Params<R> &p, cudaStream_t s, int grid) {

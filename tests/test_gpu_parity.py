@@ -117,18 +117,24 @@ def test_push_deposit_parity(env, name, prec, tol):
             assert rel_l2(g[k][live], o[k][live]) < tol, k
 
 
-def test_tiled_fixed_point_deposit_parity(env):
-    """One push/deposit step of the FP32 tiled kernel, whose shared J is a
-    fixed-point integer sum with power-of-two scales per work item (bounded
-    by |q w|, the Courant displacement and 16 x the largest particle count
-    of one cell), against the FP64 oracle: J within 1e-5 in relative L2,
-    particles as in the tail-kernel test.  (The J error of these inputs, 2e-6
-    to 8e-6, comes from the FP32 trajectories: FP32 shared atomics gave the
-    same figures to three digits.)"""
+@pytest.mark.parametrize("cluster", [False, True])
+def test_tiled_deposit_parity(env, cluster):
+    """One push/deposit step of the FP32 tiled kernel (shared-memory J with
+    FP32 shared atomics, flushed once per grid point) against the FP64
+    oracle: J within 1e-6 in relative L2 (measured 1.2e-7 to 2.8e-7), and
+    within 2e-6 with a third of the electrons, all with one momentum, piled
+    into one cell (measured up to 1.1e-6); particles as in the tail-kernel
+    test.  (An int32 fixed-point shared J, about 2^-21 of the largest
+    contribution per unit, measured 1.7e-6 to 8.7e-6 here, and 1.45e-2 with
+    a dense cell of mixed momenta.)"""
     hff, workloads, _ = env
     cfg, sim, ref = make(env, "small_hybrid", capacity=40000, precision="fp32", sort_every=4, inject=False)
     shared_initial_state(sim, ref, seed=7)
     ps = workloads.particles(cfg, n_pairs=8000, seed=23)
+    if cluster:
+        e = ps[0]
+        e["cell"][::3] = int(e["cell"][0])
+        e["ur"][::3], e["ut"][::3], e["up"][::3] = 0.3, -0.2, 0.5
     for s in range(2):
         sim.load(s, ps[s])
         ref.set_particles(s, ps[s])
@@ -136,8 +142,9 @@ def test_tiled_fixed_point_deposit_parity(env):
     sim.step_stages(1, ST["node"] | ST["push"])
     ref.step(1, ST["node"] | ST["push"])
     assert sim.info().pushed_tiled > 0
+    tol = 2e-6 if cluster else 1e-6
     for f in ("J_r", "J_th", "J_ph"):
-        assert rel_l2(sim.get(f), ref.get(f)) < 1e-5, (f, rel_l2(sim.get(f), ref.get(f)))
+        assert rel_l2(sim.get(f), ref.get(f)) < tol, (f, rel_l2(sim.get(f), ref.get(f)))
     for s in range(2):
         g, o = sim.particles(s), ref.particles(s)
         bad, ties, err = particle_mismatches(g, o, cfg["nt"])
@@ -149,13 +156,10 @@ def test_tiled_fixed_point_deposit_parity(env):
 def test_gauss_law_fp32_dense_cell(env):
     """A third of the pairs piled into one cell (each pair co-located, so
     the start is neutral), electrons with one momentum and positrons with the
-    opposite one, so that their currents add: the work items around that cell
-    take fixed-point scales about 2^7 coarser.  An overflow or a wrong scale
-    would break charge conservation at O(1); the FP32 graph path (tiled push,
-    sorts every 4 steps) keeps the Gauss residual within 1e-3 of the charge
-    density after 20 steps (measured 3.3e-4, on the polar-axis nodes, whose
-    dual volumes are the smallest; FP32 shared atomics gave the same figure,
-    and the FP64 kernels hold 1e-9), with no flag raised."""
+    opposite one, so that their currents add in that cell's shared J: the
+    FP32 graph path (tiled push, sorts every 4 steps) keeps the Gauss
+    residual within 2e-5 of the charge density after 20 steps (measured
+    4.3e-6; an int32 fixed-point shared J measured 3.3e-4), no flag raised."""
     hff, workloads, _ = env
     cfg, sim, ref = make(env, "small_pic", capacity=40000, precision="fp32", sort_every=4)
     ps = workloads.particles(cfg, n_pairs=5000, seed=61)
@@ -168,7 +172,7 @@ def test_gauss_law_fp32_dense_cell(env):
     sim.step(20)
     d, _ = sim.diagnostics()
     assert sim.info().pushed_tiled > 0
-    assert d.rho_max > 0 and d.gauss_max < 1e-3 * d.rho_max, (d.gauss_max, d.rho_max)
+    assert d.rho_max > 0 and d.gauss_max < 2e-5 * d.rho_max, (d.gauss_max, d.rho_max)
     assert sim.status() == 0
 
 
@@ -270,7 +274,9 @@ def test_diagnostics_parity(env):
 
 def test_gauss_law_fp32_graph(env):
     """Charge-conserving deposit in FP32 through the graph path: the Gauss
-    residual stays at FP32 round-off relative to the charge density."""
+    residual stays at FP32 round-off relative to the charge density, within
+    1e-6 after 20 steps (measured 1.3e-7 to 1.7e-7, the same as the untiled
+    push; an int32 fixed-point shared J measured 5.8e-5)."""
     hff, workloads, _ = env
     cfg, sim, ref = make(env, "small_pic", capacity=40000, precision="fp32", sort_every=4)
     ps = workloads.particles(cfg, n_pairs=5000, seed=61)
@@ -278,4 +284,4 @@ def test_gauss_law_fp32_graph(env):
         sim.load(s, ps[s])
     sim.step(20)
     d, _ = sim.diagnostics()
-    assert d.rho_max > 0 and d.gauss_max < 1e-4 * d.rho_max, (d.gauss_max, d.rho_max)
+    assert d.rho_max > 0 and d.gauss_max < 1e-6 * d.rho_max, (d.gauss_max, d.rho_max)
