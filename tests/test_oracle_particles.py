@@ -1,7 +1,8 @@
 """Pins of the oracle's particle side against textbook closed forms and exact
 identities (gyration, E x B drift, synchrotron cooling, straight-line motion,
-charge conservation / Gauss's law), and of the injection, the sort and the
-Philox generator against their definitions or published vectors."""
+charge conservation / Gauss's law), the removal rules (star, absorber,
+force-free cells), and of the injection, the sort and the Philox generator
+against their definitions or published vectors."""
 import math
 import os
 
@@ -232,6 +233,54 @@ def test_uperp_removed_in_surface_shell(oracle_mod):
     # direction differs by O(dt); the transverse part must be O(dt) small
     u = np.array([q["ur"][0], q["ut"][0], q["up"][0]])
     assert abs(u[2]) < 1e-2 * np.linalg.norm(u)
+
+
+def test_removal_rules(oracle_mod):
+    """Particles are removed (after depositing their last move) when they
+    reach the star, cross into the absorbing layer, or enter a cell of the
+    pure force-free domain (f = 1 at the cell's mean Psi: no particles
+    there, Sect. 3); a particle that stays in the PIC domain is kept.  The
+    removed weight is reported.  Fields: a weak radial B (B_r = 1e-6 / r^2,
+    so Psi = 1e-6 (1 - cos theta) grows with theta and no path bends within a
+    step), E = 0; f jumps from 0 to 1 between theta cells 29 and 30."""
+    cfg = pic_cfg(capacity=10, inject=False, sort_every=0)
+    nr, nt = cfg["nr"], cfg["nt"]
+    eps = 1e-6
+    tn = np.arange(nt + 1) * math.pi / nt
+    cell_psi = 0.5 * eps * (2.0 - np.cos(tn[:-1]) - np.cos(tn[1:]))
+    psi_unit = cfg["b_star"] * cfg["r_min"] ** 3 / cfg["r_lc"]
+    brk = 0.5 * (cell_psi[29] + cell_psi[30]) / psi_unit
+    cfg.update(psi_break=[brk, brk], f_break=[0.0, 1.0])
+    o = oracle_mod.Oracle(cfg)
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / nr
+    rn = cfg["r_min"] * np.exp(np.arange(nr + 1) * d)
+    for k in ("E_r", "E_th", "E_ph", "B_th", "B_ph"):
+        o.set(k, np.zeros(o.shape(k)))
+    o.set("B_r", np.repeat((eps / rn ** 2)[:, None], nt, axis=1))
+    xi_abs = math.log(cfg["r_abs"] / cfg["r_min"]) / d
+    ia = int(xi_abs)
+    # star (inward at ~c), absorber (outward at ~c, just below r_abs),
+    # force-free cell (polar motion from theta cell 29 into 30), control
+    p = dict(cell=np.array([0 * nt + 10, ia * nt + 10, 20 * nt + 29, 20 * nt + 10], np.int32),
+             xo=np.array([0.1, xi_abs - ia - 0.02, 0.5, 0.5]), yo=np.array([0.5, 0.5, 0.95, 0.5]),
+             ur=np.array([-20.0, 20.0, 0.0, 0.5]), ut=np.array([0.0, 0.0, 20.0, 0.2]),
+             up=np.array([0.0, 0.0, 0.0, 0.1]), w=np.array([1.0, 2.0, 4.0, 8.0]))
+    o.set_particles(0, p)
+    o.step(1, oracle_mod.ST["node"] | oracle_mod.ST["push"])
+    q = o.particles(0)
+    assert list(q["cell"][:3]) == [-1, -1, -1]
+    assert q["cell"][3] == 20 * nt + 10
+    dg, _ = o.diagnostics()
+    assert dg.killed == 7.0
+    # without the force-free band the third particle survives in cell 30
+    cfg.update(psi_break=[], f_break=[])
+    o2 = oracle_mod.Oracle(cfg)
+    for k in ("E_r", "E_th", "E_ph", "B_th", "B_ph"):
+        o2.set(k, np.zeros(o2.shape(k)))
+    o2.set("B_r", np.repeat((eps / rn ** 2)[:, None], nt, axis=1))
+    o2.set_particles(0, p)
+    o2.step(1, oracle_mod.ST["node"] | oracle_mod.ST["push"])
+    assert o2.particles(0)["cell"][2] == 20 * nt + 30
 
 
 def test_philox_known_answer_vectors(oracle_mod):
