@@ -263,8 +263,11 @@ def particles(cfg: dict, n_pairs: int | None = None, seed: int | None = None,
     Returns ``[electrons, positrons]``, each a dict of numpy arrays
     ``cell`` (int32, i * nt + j), ``xo``, ``yo`` (offsets in [0, 1)),
     ``ur``, ``ut``, ``up`` (u = gamma v / c in the local spherical basis) and
-    ``w`` (macro-particle weight).  Deterministic for a given seed whatever
-    the thread count."""
+    ``w`` (macro-particle weight).  The weights are those of the configured
+    count ``cfg["n_pairs"]`` (the pairs then stand for the density
+    kappa n_GJ* (r*/r)^2); drawing another ``n_pairs`` keeps the per-pair
+    weight, so the represented density scales with the number drawn.
+    Deterministic for a given seed whatever the thread count."""
     n = int(cfg["n_pairs"] if n_pairs is None else n_pairs)
     seed = int(cfg["seed"] if seed is None else seed)
     cells, sheet_cells = placement_cells(cfg)
