@@ -91,3 +91,31 @@ def test_header_is_plain_c_and_cxx(tmp_path):
                    "  (void)f;\n  return hff_plan(&c, 1, &b) == 0 ? 1 : 0;\n}\n")
     subprocess.run(["gcc", "-fsyntax-only", "-Wall", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src)],
                    check=True)
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and the field
+    offsets of its C declaration (a C program prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    structs = [hff.hff_config, hff.hff_info, hff.hff_particle_view, hff.hff_diag]
+    body = []
+    for st in structs:
+        name = st.__name__
+        body.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            body.append(f'  printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "hff.h"\nint main(void) {\n'
+                   + "\n".join(body) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
+        for f in st._fields_:
+            assert got[(st.__name__, f[0])] == getattr(st, f[0]).offset, (st.__name__, f[0])
