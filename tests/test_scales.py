@@ -1,6 +1,7 @@
 """Scale helpers against the numbers the paper prints for its reference
 millisecond pulsar (Sect. 2: P = 1 ms, B* = 1e7 G, r* = 1e6 cm; Sect. 5.1 and
-Table 1 for the 8192^2 run with R_LC = 5e6 cm, r_max = (10/3) R_LC)."""
+Table 1 for the 8192^2 run with R_LC = 5e6 cm, r_max = (10/3) R_LC), and the
+monopole run's B_ph diagnostic against Michel's solution (Sect. 4)."""
 import math
 
 import pytest
@@ -66,3 +67,33 @@ def test_code_units():
     # e Phi_pc / m_e = gamma_pc in code units
     assert close((1.0 / cu["r_lc"] ** 2) / cu["m_e"], cu["gamma_pc"], 1e-12)
     assert cu["gamma_th"] > cu["gamma_s"] > 1.0
+
+
+def test_monopole_bphi_error_against_michel():
+    """The monopole run's B_ph diagnostic: zero for Michel's own field
+    -(Psi*/R_LC) sin(theta)/r at the half nodes, 0.1 for a field 10% too
+    strong in one hemisphere, per hemisphere."""
+    import numpy as np
+    from paper_2406_14512_gb300 import monopole
+    cfg = monopole.config(64)
+    nr, nt = cfg["nr"], cfg["nt"]
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / nr
+    rh = cfg["r_min"] * np.exp((np.arange(nr) + 0.5) * d)
+    th = (np.arange(nt) + 0.5) * math.pi / nt
+    psi_star = cfg["b_star"] * cfg["r_min"] ** 2
+    exact = -(psi_star / cfg["r_lc"]) * np.sin(th)[None, :] / rh[:, None]
+
+    class Fake:
+        def __init__(self, f):
+            self.f = f
+
+        def get(self, name):
+            assert name == "B_ph"
+            return self.f
+
+    e = monopole.bphi_error(Fake(exact.astype(np.float32)), cfg)
+    assert e["north_pic"] < 1e-6 and e["south_ff"] < 1e-6
+    f = exact.copy()
+    f[:, th > math.pi / 2] *= 1.1
+    e = monopole.bphi_error(Fake(f), cfg)
+    assert e["north_pic"] < 1e-12 and abs(e["south_ff"] - 0.1) < 1e-12
