@@ -112,6 +112,8 @@ def lib():
         L.or_move_local.argtypes = [d, d, d, pd, pd, pd, pd, pd]
         L.or_blend.restype = d
         L.or_blend.argtypes = [vp, d]
+        L.or_gather.argtypes = [vp, i32, i32, d, d, pd, pd]
+        L.or_deposit.argtypes = [vp, d, i32, i32, d, d, d, d, d]
         L.or_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                        C.POINTER(C.c_uint32)]
         _lib = L
@@ -264,6 +266,17 @@ class Oracle:
 
     def blend(self, psi: float) -> float:
         return self.L.or_blend(self.h, psi)
+
+    def gather(self, i: int, j: int, xo: float, yo: float):
+        """(E, B) in the local spherical basis at offset (xo, yo) of cell (i, j)."""
+        e, b = (C.c_double * 3)(), (C.c_double * 3)()
+        self.L.or_gather(self.h, i, j, xo, yo, e, b)
+        return np.array(e[:]), np.array(b[:])
+
+    def deposit(self, qw: float, i0: int, j0: int, x0: float, y0: float, x1: float, y1: float,
+                vphi: float) -> None:
+        """One charge-conserving deposit into J_r, J_th, J_ph (added)."""
+        self.L.or_deposit(self.h, qw, i0, j0, x0, y0, x1, y1, vphi)
 
     def surface_counts(self) -> np.ndarray:
         return np.array([self.L.or_surface_count(self.h, j) for j in range(self.nt)], np.int32)

@@ -664,6 +664,17 @@ static void deposit(ost *s, double qw, int i0, int j0, double x0, double y0, dou
     }
 }
 
+/* The gather at one position and one deposit into J_PIC, exactly as the
+ * push calls them; exported for the pins of the interpolation and of the
+ * azimuthal current (tests only).                                           */
+void or_gather(void *st, int32_t i, int32_t j, double xo, double yo, double e[3], double b[3]) {
+  gather((const ost *)st, i, j, xo, yo, e, b);
+}
+void or_deposit(void *st, double qw, int32_t i0, int32_t j0, double x0, double y0, double x1,
+                double y1, double vphi) {
+  deposit((ost *)st, qw, i0, j0, x0, y0, x1, y1, vphi);
+}
+
 static double cell_psi(const ost *s, int i, int j) {
   return 0.25 * (PSI(i, j) + PSI(i + 1, j) + PSI(i, j + 1) + PSI(i + 1, j + 1));
 }

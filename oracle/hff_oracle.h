@@ -145,6 +145,14 @@ void or_push_local(double qm, double krr, double dt, const double u[3],
 void or_move_local(double r, double th, double dt, const double u[3],
                    double *dr, double *dth, double *dphi, double u_out[3]);
 double or_blend(void *st, double psi);
+/* The linear gather of E and B at offset (xo, yo) of cell (i, j), and one
+ * charge-conserving deposit of charge qw moving from (x0, y0) to (x1, y1)
+ * (logical coordinates relative to node (i0, j0)) with azimuthal velocity
+ * vphi, added to J_r, J_th, J_ph, as the push performs them. */
+void or_gather(void *st, int32_t i, int32_t j, double xo, double yo, double e[3], double b[3]);
+void or_deposit(void *st, double qw, int32_t i0, int32_t j0, double x0, double y0, double x1,
+                double y1, double vphi);
+
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                       uint32_t out[4]);
 
