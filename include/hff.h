@@ -217,7 +217,9 @@ int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, voi
 /* Replace the particles of one species by n particles (SoA arrays as described
  * above; `where` = HFF_HOST or HFF_DEVICE says where the source arrays live).
  * Values must be in the configured precision.  The particles are sorted by
- * tile if sorting is enabled.  HFF_ERR_CAPACITY if n > capacity. */
+ * tile if sorting is enabled.  HFF_ERR_CAPACITY if n > capacity.  A cell
+ * index at or past nr * nt is invalid: the load completes with those
+ * particles removed and returns HFF_ERR_ARG. */
 int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const int32_t *cell,
                        const void *xo, const void *yo, const void *ur, const void *ut,
                        const void *up, const void *w, int where);
@@ -266,8 +268,9 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof);
 /* Step counter, time step, counts and the tile / precision choices. */
 int hff_get_info(hff_handle *h, hff_info *out);
 
-/* Read and clear the latched device status: HFF_OK, HFF_ERR_CAPACITY or
- * HFF_ERR_NONFINITE.  Synchronises the stream. */
+/* Read and clear the latched device status: HFF_OK, HFF_ERR_CAPACITY,
+ * HFF_ERR_NONFINITE or HFF_ERR_ARG (a particle with a cell index outside the
+ * grid met by a sort, and removed).  Synchronises the stream. */
 int hff_status(hff_handle *h);
 
 /* Release the handle and its CUDA graphs (not the caller's memory). */
@@ -327,11 +330,14 @@ int hff_checkpoint_load(hff_handle *h, int inst, const void *src, size_t bytes);
  * Scratch lives in one fixed device array per GPU (about 4.3 MB), reserved in
  * every process that loads the library until it exits; nothing is allocated.
  * The first call on a device looks up that array's device address, so make
- * it before any stream capture.  Calls share the array: calls that overlap on
- * the GPU (other streams, threads) race and must be serialised by the caller.
+ * it before any stream capture.  Every call synchronises `stream` to read the
+ * live count back, so no call can be made while the stream is being
+ * captured.  Calls share the array: calls that overlap on the GPU (other
+ * streams, threads) race and must be serialised by the caller.
  * Returns HFF_ERR_CAPACITY if n > HFF_NOALLOC_MAX_PARTICLES, HFF_ERR_ARG for
- * invalid arguments, HFF_ERR_CUDA if a CUDA call fails; the message is given
- * by hff_noalloc_last_error(). */
+ * invalid arguments or a cell index at or past nr * nt (such a particle is
+ * ordered with the removed ones), HFF_ERR_CUDA if a CUDA call fails; the
+ * message is given by hff_noalloc_last_error(). */
 #define HFF_NOALLOC_MAX_PARTICLES 262144
 int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr, int32_t nt, int32_t tile_r,
                            int32_t tile_t, uint32_t *order, int64_t *n_live, void *stream);

@@ -1052,15 +1052,27 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
   }
   if (h->c.capacity > n)
     CK(cudaMemsetAsync(h->base + h->o.part[pp][species][0] + n * 4, 0xFF, (h->c.capacity - n) * 4, h->st));
+  // a cell index at or past nr * nt is invalid input: that particle is
+  // removed (cell = -1) and the load reports HFF_ERR_ARG after completing
+  launch_check_cells(reinterpret_cast<int32_t *>(h->base + h->o.part[pp][species][0]), n,
+                     (int64_t)h->c.nr * h->c.nt, &h->small->status, h->st);
   const long long nn = n, zero = 0;
   CK(cudaMemcpyAsync(&h->small->count[species], &nn, sizeof(nn), cudaMemcpyHostToDevice, h->st));
   CK(cudaMemcpyAsync(&h->small->count_sorted[species], &zero, sizeof(zero), cudaMemcpyHostToDevice, h->st));
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, &h->small->status, sizeof(st), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  if (st & kStBadCell) {  // clear this bit only; other latched errors stay for hff_status
+    const unsigned rest = st & ~kStBadCell;
+    CK(cudaMemcpyAsync(&h->small->status, &rest, sizeof(rest), cudaMemcpyHostToDevice, h->st));
+  }
   if (h->c.sort_every > 0) {
     const int rc = h->c.precision == HFF_FP64 ? run_sort_now<double>(h, h->st) : run_sort_now<float>(h, h->st);
     if (rc != HFF_OK) return rc;
-    CK(cudaStreamSynchronize(h->st));
   }
+  CK(cudaStreamSynchronize(h->st));
+  if (st & kStBadCell)
+    return fail(HFF_ERR_ARG, "a particle cell index is at or past nr * nt; such particles were removed");
   return HFF_OK;
 }
 
@@ -1335,6 +1347,7 @@ int hff_status(hff_handle *h) {
   if (st & kStWorklist) return fail(HFF_ERR_CAPACITY, "work list overflow");
   if (st & kStNonfinite) return fail(HFF_ERR_NONFINITE, "non-finite particle state removed");
   if (st & kStNonfiniteField) return fail(HFF_ERR_NONFINITE, "non-finite field values (seen by hff_diagnostics)");
+  if (st & kStBadCell) return fail(HFF_ERR_ARG, "a particle cell index outside the grid was removed");
   return HFF_OK;
 }
 

@@ -37,6 +37,7 @@ constexpr unsigned kStCapacity = 1u;
 constexpr unsigned kStNonfinite = 2u;
 constexpr unsigned kStWorklist = 4u;
 constexpr unsigned kStNonfiniteField = 8u;
+constexpr unsigned kStBadCell = 16u;   // a loaded cell index outside the grid
 
 template <typename R>
 struct Tables {
@@ -213,6 +214,8 @@ template <typename R> void launch_sort_species(const Params<R> &p, int species, 
                                                const SortScratch &ss, cudaStream_t s, bool gather);
 // the deferred payload gather of a species, src -> sp by sidx (slots < count)
 template <typename R> void launch_materialize(const Params<R> &p, int species, cudaStream_t s);
+// loaded cells at or past ncells become removed particles; kStBadCell latched
+void launch_check_cells(int32_t *cell, int64_t n, int64_t ncells, unsigned *status, cudaStream_t s);
 template <typename R> void launch_worklist(const Params<R> &p, const SortScratch *ss,
                                            const WorkList &wl, int species, int first,
                                            cudaStream_t s);

@@ -3,13 +3,16 @@
 // of the tiled push.
 //
 // Key = tile index (cells grouped in tile_r x tile_t blocks, row-major over
-// tiles); removed particles get the key ntiles and sort last.  The sort is an
+// tiles); removed particles get the key ntiles and sort last, and so does a
+// cell index outside the grid (never produced by the push; only a caller's
+// input can hold one), which is also reported through a flag word.  The sort is an
 // LSD radix sort over 8-bit digits of (key, index) pairs.  Each pass: per-block
 // digit histograms (2048 elements per block), one exclusive scan over the
 // digit-major histogram matrix, and a stable scatter in which every element's
 // rank inside its block comes from warp match masks, so equal keys keep their
 // order (the result equals a stable sort by key).  The particle payload moves
 // once, in a final gather.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/hff.h"
@@ -23,8 +26,8 @@ constexpr int kSortBlock = kSortThreads * kSortItems;  // 2048 elements
 constexpr int kScanBlock = 4096;
 
 __device__ __forceinline__ uint32_t tile_key(int cell, int nt, int tile_r, int tile_t, int ntt,
-                                             uint32_t dead) {
-  if (cell < 0) return dead;
+                                             int64_t ncells, uint32_t dead) {
+  if (cell < 0 || cell >= ncells) return dead;
   const int i = cell / nt, j = cell - (cell / nt) * nt;
   return (uint32_t)((i / tile_r) * ntt + j / tile_t);
 }
@@ -36,13 +39,16 @@ struct SortArgs {
   uint32_t *keys_out, *idx_out;
   uint32_t *hist;
   int64_t n;
+  int64_t ncells;           // nr * nt: larger cell indices are invalid input
+  unsigned *bad;            // flag word: bad_bit is or-ed in for an invalid cell
+  unsigned bad_bit;
   int nb, shift, nt, tile_r, tile_t, ntt;
   uint32_t dead;
   bool first;
 };
 
 __device__ __forceinline__ uint32_t load_key(const SortArgs &a, int64_t e) {
-  return a.first ? tile_key(a.cell[e], a.nt, a.tile_r, a.tile_t, a.ntt, a.dead) : a.keys_in[e];
+  return a.first ? tile_key(a.cell[e], a.nt, a.tile_r, a.tile_t, a.ntt, a.ncells, a.dead) : a.keys_in[e];
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
@@ -50,10 +56,15 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+  bool bad = false;
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t e = base + r * kSortThreads + threadIdx.x;
-    if (e < a.n) atomicAdd(&h[(load_key(a, e) >> a.shift) & 255u], 1u);
+    if (e < a.n) {
+      atomicAdd(&h[(load_key(a, e) >> a.shift) & 255u], 1u);
+      if (a.first && a.cell[e] >= a.ncells) bad = true;
+    }
   }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(a.bad, a.bad_bit);
   __syncthreads();
   a.hist[(int64_t)threadIdx.x * a.nb + blockIdx.x] = h[threadIdx.x];
 }
@@ -322,6 +333,9 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
   SortArgs a{};
   a.cell = p.sp[s].cell;
   a.n = n;
+  a.ncells = (int64_t)p.nr * p.nt;
+  a.bad = p.status;
+  a.bad_bit = kStBadCell;
   a.nb = nb;
   a.nt = p.nt; a.tile_r = p.tile_r; a.tile_t = p.tile_t; a.ntt = p.ntt;
   a.dead = dead;
@@ -355,6 +369,19 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
   }
 }
 
+// Loaded particles: a cell index at or past nr * nt is invalid input; the
+// particle is removed (cell = -1) and kStBadCell latched.
+__global__ void k_check_cells(int32_t *cell, int64_t n, int64_t ncells, unsigned *status) {
+  bool bad = false;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    if (cell[q] >= ncells) { cell[q] = -1; bad = true; }
+  if (bad) atomicOr(status, kStBadCell);
+}
+
+void launch_check_cells(int32_t *cell, int64_t n, int64_t ncells, unsigned *status, cudaStream_t st) {
+  if (n > 0) k_check_cells<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(cell, n, ncells, status);
+}
+
 template <typename R>
 void launch_materialize(const Params<R> &p, int s, cudaStream_t st) {
   k_gather_live<R><<<1216, 256, 0, st>>>(p.src[s], p.sp[s], p.sidx[s], p.count, s);
@@ -386,7 +413,8 @@ constexpr int64_t kMaxN = HFF_NOALLOC_MAX_PARTICLES;
 constexpr int64_t kMaxBlocks = (kMaxN + kSortBlock - 1) / kSortBlock;
 constexpr int64_t kMaxHist = kMaxBlocks * 256;
 constexpr int64_t kMaxParts = (kMaxHist + kScanBlock - 1) / kScanBlock;
-// keys_a | keys_b | idx_a | idx_b | histogram | block sums | live count
+// keys_a | keys_b | idx_a | idx_b | histogram | block sums | live count,
+// invalid-cell flag
 constexpr int64_t kWords = 4 * kMaxN + kMaxHist + kMaxParts + 64;
 
 // One copy per device, alive until the process exits; shared by every call.
@@ -396,7 +424,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t *g_addr[kMaxDevices] = {};
 
-__global__ void k_live_init(uint32_t *live, uint32_t n) { *live = n; }
+// live count and invalid-cell flag: written afresh at the start of every call
+__global__ void k_live_init(uint32_t *live, uint32_t n) {
+  live[0] = n;
+  live[1] = 0u;
+}
 
 // first slot holding a removed particle (keys are sorted, removed ones last)
 __global__ void k_live_count(const uint32_t *keys, int64_t n, uint32_t dead, uint32_t *live) {
@@ -415,6 +447,9 @@ extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr
                                       int32_t tile_t, uint32_t *order, int64_t *n_live, void *stream) {
   using namespace hff;
   using namespace hff::noalloc;
+  // an error left by earlier, unrelated work would otherwise be reported
+  // (and cleared) by the check after this call's launches
+  (void)cudaGetLastError();
   if (n < 0 || nr < 1 || nt < 1 || tile_r < 1 || tile_t < 1 || !n_live || (n > 0 && (!cell || !order))) {
     hff_noalloc_err = "hff_tile_order_noalloc: invalid argument";
     return HFF_ERR_ARG;
@@ -455,6 +490,7 @@ extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr
   const uint32_t dead = (uint32_t)ntiles;
   if (n == 0) {
     *n_live = 0;
+    hff_noalloc_err = "";
     return HFF_OK;
   }
   const int nbits = bits_for(dead), passes = (nbits + 7) / 8;
@@ -464,10 +500,14 @@ extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr
   SortArgs a{};
   a.cell = cell;
   a.n = n;
+  a.ncells = (int64_t)nr * nt;
+  a.bad = live + 1;
+  a.bad_bit = 1u;
   a.nb = nb;
   a.nt = nt; a.tile_r = tile_r; a.tile_t = tile_t; a.ntt = ntt;
   a.dead = dead;
   a.hist = hist;
+  k_live_init<<<1, 1, 0, st>>>(live, (uint32_t)n);
   uint32_t *ko = keys_a, *io = idx_a, *ki = keys_b, *ii = idx_b;
   for (int pass = 0; pass < passes; ++pass) {
     a.first = (pass == 0);
@@ -482,18 +522,21 @@ extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr
     uint32_t *t = ki; ki = ko; ko = t;
     t = ii; ii = io; io = t;
   }
-  // the live count is written afresh by every call (previous contents of
-  // the shared array are never read)
-  k_live_init<<<1, 1, 0, st>>>(live, (uint32_t)n);
+  // the live count and the flag were written at the start of this call
+  // (previous contents of the shared array are never read)
   k_live_count<<<(int)((n + 255) / 256), 256, 0, st>>>(ki, n, dead, live);
-  uint32_t h_live = 0;
+  uint32_t h_live[2] = {0u, 0u};
   if (cudaMemcpyAsync(order, ii, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(&h_live, live, sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(h_live, live, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     hff_noalloc_err = "hff_tile_order_noalloc: a CUDA call failed";
     return HFF_ERR_CUDA;
   }
-  *n_live = (int64_t)h_live;
+  if (h_live[1]) {
+    hff_noalloc_err = "hff_tile_order_noalloc: a cell index is at or past nr * nt (ordered as removed)";
+    return HFF_ERR_ARG;
+  }
+  *n_live = (int64_t)h_live[0];
   hff_noalloc_err = "";
   return HFF_OK;
 }

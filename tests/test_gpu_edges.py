@@ -39,6 +39,28 @@ def test_no_particles_zero_capacity(env):
     assert sim.status() == 0 and sim.info().count[0] == 0
 
 
+def test_cell_outside_the_grid_is_rejected_on_load(env):
+    """A caller's cell index at or past nr * nt is invalid: the load removes
+    that particle, keeps the others in tile order and returns HFF_ERR_ARG;
+    the instance then steps normally."""
+    hff, workloads, _ = env
+    for sort_every in (4, 0):
+        cfg = workloads.config("small_hybrid")
+        cfg.update(capacity=4000, inject=False, sort_every=sort_every)
+        p = {k: v.copy() for k, v in workloads.particles(cfg, n_pairs=1500, seed=11)[0].items()}
+        ncell = cfg["nr"] * cfg["nt"]
+        p["cell"][[3, 500]] = [ncell, ncell + 12345]
+        sim = hff.Sim(cfg)
+        with pytest.raises(hff.HffError) as e:
+            sim.load(0, p)
+        assert e.value.code == hff.HFF_ERR_ARG
+        got = sim.particles(0)
+        assert int((got["cell"] >= 0).sum()) == 1498 and got["cell"].max() < ncell
+        sim.step(3)
+        assert sim.status() == 0
+        sim.close()
+
+
 def test_capacity_overflow_is_latched(env):
     hff, workloads, _ = env
     cfg = workloads.config("small_pic")

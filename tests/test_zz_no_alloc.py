@@ -60,3 +60,24 @@ def test_noalloc_rejects_oversized_input(env):
         hff.hff_tile_order_noalloc(cell.data_ptr(), n, 64, 64, 8, 8, order.data_ptr(),
                                    torch.cuda.current_stream().cuda_stream)
     assert e.value.code == hff.HFF_ERR_CAPACITY
+
+
+def test_noalloc_rejects_a_cell_outside_the_grid(env):
+    """A cell index at or past nr * nt orders as removed and the call reports
+    HFF_ERR_ARG; a valid call right after it still matches the load order."""
+    torch, hff, _ = env
+    nr, nt = 64, 48
+    cell = torch.arange(0, 3000, dtype=torch.int32, device="cuda")
+    cell[17] = nr * nt + 5
+    order = torch.empty(3000, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(hff.HffError) as e:
+        hff.hff_tile_order_noalloc(cell.data_ptr(), 3000, nr, nt, 8, 8, order.data_ptr(), st)
+    assert e.value.code == hff.HFF_ERR_ARG
+    assert int(order[2999].item()) == 17           # ordered last, with the removed ones
+    cell[17] = 17
+    live = hff.hff_tile_order_noalloc(cell.data_ptr(), 3000, nr, nt, 8, 8, order.data_ptr(), st)
+    assert live == 3000
+    c = cell.cpu().numpy()
+    key = (c // nt // 8) * ((nt + 7) // 8) + (c % nt) // 8
+    assert np.array_equal(order.cpu().numpy(), np.argsort(key, kind="stable"))
