@@ -5,8 +5,11 @@
  *
  * One call of hff_step advances one or more magnetospheres by whole time
  * steps on the GPU:
- *   - flux function Psi as a theta-prefix of B_r (Sect. 3, Eq. 27), FP64
- *   - blend mask f(Psi) (Eqs. 29-31 generalised to a piecewise-linear table)
+ *   - flux function Psi as a theta-prefix of B_r (Sect. 3, Eq. 27): FP64 in
+ *     FP64 instances, a float pair of about 48 significant bits summed from
+ *     exact products in FP32 instances
+ *   - blend mask f(Psi) (Eqs. 29-31 generalised to a piecewise-linear table),
+ *     the segment chosen by comparisons at that precision
  *   - force-free perpendicular current (first term of Eq. 24)
  *   - modified Boris push with radiation reaction (Eqs. 15-17), move,
  *     charge-conserving deposit of J_PIC
@@ -29,6 +32,11 @@
  *   9      Psi at the nodes        (nr+1) x (nt+1), always FP64
  *   10..12 J_perp at the nodes     (nr+1) x (nt+1)
  *   13..15 Delta E at the nodes    (nr+1) x (nt+1)
+ *   16     f at the E_r edges      nr     x (nt+1)   (Eqs. 29-31; read only)
+ *   17     f at the E_th edges     (nr+1) x nt
+ *   18     f at the nodes (E_ph)   (nr+1) x (nt+1)
+ *   19     force-free cell flags   nr     x nt, one byte each (1 = f >= 1 at
+ *          the mean Psi of the cell's corners: no particles, Eq. 29)
  * Field values are FP32 (HFF_FP32) or FP64 (HFF_FP64) as configured.
  *
  * Particles (per species, structure of arrays): int32 cell = i * nt + j
@@ -232,9 +240,11 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
  * is not changed. */
 int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where);
 
-/* Copy field `which` (0..15, see the table above) into dst (host or device,
+/* Copy field `which` (0..19, see the table above) into dst (host or device,
  * `bytes` must equal the field size).  which = 9 computes Psi (Eq. 27) in FP64
- * from the current B_r.  Synchronises the stream. */
+ * from the current B_r.  which = 16..19 compute the blend weights from the
+ * current B exactly as the next step's node pass does (the step's own flux
+ * prefix and comparisons).  Synchronises the stream. */
 int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int where);
 
 /* Advance nsteps whole steps (asynchronous on the stream; one CUDA graph per

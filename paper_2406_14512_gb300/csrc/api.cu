@@ -144,6 +144,7 @@ struct Offsets {
   size_t tab_r[16];      // rn inv_rn rh inv_rh c_b2 c_bp2 c_e2 c_ep2 rho_a rho_b rh2 dep_r dep_t dep_p sig_n sig_h
   size_t tab_c[6];       // sn sh inv_sh inv_dcp inv_dch cn
   size_t r2n, dcp;       // FP64 prefix factors
+  size_t dcp2;           // dcp as normalised float pairs (FP32 prefix)
   size_t dg[9];          // FP64 diag geometry: rn rh rlo rhi sn sh dch tlo thi
   size_t part[2][kMaxSpecies][7];
   size_t small;          // counters block
@@ -186,7 +187,8 @@ void layout(const hff_config &c, Offsets &o) {
   const size_t sz[22] = {nr * (nt + 1), (nr + 1) * nt, nn, (nr + 1) * nt, nr * (nt + 1), nr * nt,
                          (nr + 1) * nt, nr * (nt + 1), nr * nt, nr * (nt + 1), (nr + 1) * nt, nn,
                          nn, nn, nn, nn, nn, nn, nn, nr * (nt + 1), (nr + 1) * nt, nn};
-  for (int k = 0; k < 22; ++k) o.f[k] = L.take(sz[k] * R);
+  // Psi (slot 12) is FP64 or a float pair: 8 bytes per node either way
+  for (int k = 0; k < 22; ++k) o.f[k] = L.take(sz[k] * (k == 12 ? 8 : R));
   o.ffcell = L.take(nr * nt);
   const size_t rl[16] = {nr + 1, nr + 1, nr, nr, nr, nr, nr + 1, nr + 1, nr + 1, nr + 1, nr, nr, nr + 1, nr + 1, nr + 1, nr};
   for (int k = 0; k < 16; ++k) o.tab_r[k] = L.take(rl[k] * R);
@@ -194,6 +196,7 @@ void layout(const hff_config &c, Offsets &o) {
   for (int k = 0; k < 6; ++k) o.tab_c[k] = L.take(cl[k] * R);
   o.r2n = L.take((nr + 1) * 8);
   o.dcp = L.take(nt * 8);
+  o.dcp2 = L.take(nt * 8);
   const size_t dl[9] = {nr + 1, nr, nr + 1, nr + 1, nt + 1, nt, nt + 1, nt + 1, nt + 1};
   for (int k = 0; k < 9; ++k) o.dg[k] = L.take(dl[k] * 8);
   const size_t cap = (size_t)c.capacity;
@@ -283,6 +286,11 @@ template <typename R> Params<R> *params(hff_handle *h);
 template <> Params<float> *params<float>(hff_handle *h) { return h->pf; }
 template <> Params<double> *params<double>(hff_handle *h) { return h->pd; }
 
+// a breakpoint of Eqs. 29-31 in the representation of Psi
+template <typename R> typename PsiOf<R>::T psi_value(double x);
+template <> double psi_value<double>(double x) { return x; }
+template <> float2 psi_value<float>(double x) { return psi_pair_of(x); }
+
 template <typename R>
 void fill_params(hff_handle *h) {
   const hff_config &c = h->c;
@@ -306,8 +314,11 @@ void fill_params(hff_handle *h) {
     }
     p.n_breaks = c.n_breaks;
     for (int k = 0; k < kMaxBreaks; ++k) {
-      p.psi_break[k] = (R)(c.psi_break[k] * h->psi_unit);
+      const double x = c.psi_break[k] * h->psi_unit;
+      p.psi_bk[k] = psi_value<R>(x);
       p.f_break[k] = (R)c.f_break[k];
+      const double x0 = k > 0 ? c.psi_break[k - 1] * h->psi_unit : x;
+      p.f_slope[k] = (k > 0 && x > x0) ? (R)((c.f_break[k] - c.f_break[k - 1]) / (x - x0)) : R(0);
     }
     p.n_species = c.n_species;
     for (int s = 0; s < c.n_species; ++s) {
@@ -331,10 +342,13 @@ void fill_params(hff_handle *h) {
     for (int k = 0; k < 6; ++k) *tc[k] = reinterpret_cast<const R *>(b + o.tab_c[k]);
     t.r2n = reinterpret_cast<const double *>(b + o.r2n);
     t.dcp = reinterpret_cast<const double *>(b + o.dcp);
+    t.dcp2 = reinterpret_cast<const float2 *>(b + o.dcp2);
     Fields<R> &f = p.f;
     R **fp[22] = {&f.er, &f.et, &f.ep, &f.br, &f.bt, &f.bp, &f.br0, &f.bt0, &f.bp0, &f.jr, &f.jt, &f.jp,
-                  &f.psi, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep, &f.sr, &f.st, &f.sp};
-    for (int k = 0; k < 22; ++k) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
+                  nullptr, &f.jpr, &f.jpt, &f.jpp, &f.der, &f.det, &f.dep, &f.sr, &f.st, &f.sp};
+    for (int k = 0; k < 22; ++k)
+      if (fp[k]) *fp[k] = reinterpret_cast<R *>(b + o.f[k]);
+    f.psi = reinterpret_cast<typename PsiOf<R>::T *>(b + o.f[12]);
     f.ffcell = reinterpret_cast<uint8_t *>(b + o.ffcell);
     const int pp = (c.sort_every > 0) ? par : 0, po = (c.sort_every > 0) ? par ^ 1 : 0;
     for (int s = 0; s < c.n_species; ++s) {
@@ -454,6 +468,12 @@ int init_state(hff_handle *h) {
   for (int j = 0; j < nt; ++j) dcp.push_back(g.dcp(j));
   if ((rc = upload_d(h, h->o.r2n, r2n)) != HFF_OK) return rc;
   if ((rc = upload_d(h, h->o.dcp, dcp)) != HFF_OK) return rc;
+  {  // the same factors as normalised float pairs, for the FP32 prefix
+    std::vector<float2> d2(nt);
+    for (int j = 0; j < nt; ++j) d2[j] = psi_pair_of(dcp[j]);
+    CK(cudaMemcpyAsync(h->base + h->o.dcp2, d2.data(), d2.size() * sizeof(float2), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+  }
   {  // FP64 diagnostic geometry
     std::vector<double> D[9];
     for (int i = 0; i <= nr; ++i) { D[0].push_back(g.rn(i)); D[2].push_back(g.rlo(i)); D[3].push_back(g.rhi(i)); }
@@ -1087,13 +1107,20 @@ static void combine_field(hff_handle *h, void *dst, const void *a, size_t b_off,
 static int64_t field_elems(const hff_handle *h, int which) {
   const int64_t nr = h->c.nr, nt = h->c.nt;
   switch (which) {
-    case 0: case 6: return nr * (nt + 1);
-    case 1: case 7: return (nr + 1) * nt;
+    case 0: case 6: case 16: return nr * (nt + 1);
+    case 1: case 7: case 17: return (nr + 1) * nt;
     case 3: return (nr + 1) * nt;
     case 4: return nr * (nt + 1);
-    case 5: return nr * nt;
+    case 5: case 19: return nr * nt;
     default: return (nr + 1) * (nt + 1);
   }
+}
+
+// bytes of one element of output `which` of hff_fields
+static size_t field_elem_bytes(const hff_handle *h, int which) {
+  if (which == 9) return 8;
+  if (which == 19) return 1;
+  return h->c.precision == HFF_FP64 ? 8 : 4;
 }
 
 int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where) {
@@ -1118,12 +1145,32 @@ int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t by
 
 int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int where) {
   h = member(h, inst);
-  if (!h || which < 0 || which > 15 || !dst) return fail(HFF_ERR_ARG, "bad arguments");
-  const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
-  const size_t want = (size_t)field_elems(h, which) * (which == 9 ? 8 : R);
+  if (!h || which < 0 || which > 19 || !dst) return fail(HFF_ERR_ARG, "bad arguments");
+  const size_t want = (size_t)field_elems(h, which) * field_elem_bytes(h, which);
   if (bytes != want) return fail(HFF_ERR_ARG, "byte count does not match the field");
   const cudaMemcpyKind kind = where == HFF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (which == 9) {
+  if (which >= 16) {
+    // the blend weights from the current B, as the next step's node pass
+    // computes them: the step's own flux prefix, then f on request, staged in
+    // the FP64 node scratch (room for f at the three locations and the flags)
+    const int rc = materialize_any(h);
+    if (rc != HFF_OK) return rc;
+    // one output at a time, staged in the FP64 node scratch (>= any of them)
+    char *sc = h->base + h->o.psi64;
+    void *o[4] = {nullptr, nullptr, nullptr, nullptr};
+    o[which - 16] = sc;
+    if (h->c.precision == HFF_FP64) {
+      launch_psi<double>(h->pd[h->parity], h->st);
+      launch_blend_out<double>(h->pd[h->parity], (double *)o[0], (double *)o[1], (double *)o[2], (uint8_t *)o[3],
+                               h->st);
+    } else {
+      launch_psi<float>(h->pf[h->parity], h->st);
+      launch_blend_out<float>(h->pf[h->parity], (float *)o[0], (float *)o[1], (float *)o[2], (uint8_t *)o[3],
+                              h->st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, sc, bytes, kind, h->st));
+  } else if (which == 9) {
     double *psi = reinterpret_cast<double *>(h->base + h->o.psi64);
     if (h->c.precision == HFF_FP64) launch_psi64<double>(h->pd[0], psi, h->st);
     else launch_psi64<float>(h->pf[0], psi, h->st);

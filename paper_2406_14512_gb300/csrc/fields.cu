@@ -29,27 +29,39 @@ constexpr int kRowThreads = 128;
 // the threads of a warp, each walking its own contiguous chunk, hit distinct
 // banks.
 //
-// Accumulation: FP64 for FP64 instances.  For FP32 instances a compensated
-// pair of floats (Knuth's two-sum: the rounding error of every addition is
-// carried in a second float), about 44 significant bits, far below the FP32
-// rounding of the stored prefix and at FP32 instead of FP64 throughput.
+// Accumulation: FP64 for FP64 instances.  For FP32 instances every term is
+// formed exactly as a float pair (B_r = B_0 + dB by two-sum, times the FP64
+// face factor held as a float pair, the product by fma) and summed in a
+// compensated pair (the rounding error of every addition carried in a second
+// float); the prefix leaves the kernel as a normalised pair, about 48
+// significant bits, at FP32 instead of FP64 throughput.
 constexpr int kPsiThreads = 256;
 __host__ __device__ __forceinline__ int psi_pad(int j) { return j + (j >> 5); }
 
 struct Acc64 {
+  using Term = double;
   double v;
   __device__ __forceinline__ void add(double x) { v += x; }
   __device__ __forceinline__ void add(const Acc64 &o) { v += o.v; }
   __device__ __forceinline__ Acc64 neg() const { return {-v}; }
   __device__ __forceinline__ Acc64 shfl_up(int o) const { return {__shfl_up_sync(0xffffffffu, v, o)}; }
   __device__ __forceinline__ double times(double r2) const { return r2 * v; }
+  static __device__ __forceinline__ double term(const Params<double> &p, double b0, double db, int j) {
+    return (b0 + db) * p.t.dcp[j];
+  }
+  static __device__ __forceinline__ double zero() { return 0.0; }
 };
 struct Acc32x2 {
+  using Term = float2;
   float hi, lo;
   __device__ __forceinline__ void add(float x) {
-    const float s = hi + x, bv = s - hi;
-    lo += (hi - (s - bv)) + (x - bv);
-    hi = s;
+    const float2 s = two_sum(hi, x);
+    hi = s.x;
+    lo += s.y;
+  }
+  __device__ __forceinline__ void add(float2 t) {
+    add(t.x);
+    lo += t.y;
   }
   __device__ __forceinline__ void add(const Acc32x2 &o) {
     add(o.hi);
@@ -59,25 +71,44 @@ struct Acc32x2 {
   __device__ __forceinline__ Acc32x2 shfl_up(int o) const {
     return {__shfl_up_sync(0xffffffffu, hi, o), __shfl_up_sync(0xffffffffu, lo, o)};
   }
-  // (hi + lo) * r2 with r2 split into two floats: one final rounding
-  __device__ __forceinline__ float times(double r2) const {
-    const float r2h = (float)r2, r2l = (float)(r2 - (double)r2h);
-    return fmaf(hi, r2h, fmaf(hi, r2l, lo * r2h));
+  // (hi + lo) (r2h + r2l) as a normalised pair (r2 split on the host side of
+  // the loop)
+  __device__ __forceinline__ float2 times2(float r2h, float r2l) const {
+    const float ph = hi * r2h;
+    const float pe = fmaf(hi, r2h, -ph) + fmaf(hi, r2l, lo * r2h);
+    const float h = ph + pe;
+    return make_float2(h, pe - (h - ph));
   }
+  // (b0 + db) * dcp_j: the sum exactly by two-sum, the product by fma
+  static __device__ __forceinline__ float2 term(const Params<float> &p, float b0, float db, int j) {
+    const float2 b = two_sum(b0, db), d = p.t.dcp2[j];
+    const float ph = b.x * d.x;
+    return make_float2(ph, fmaf(b.x, d.x, -ph) + fmaf(b.x, d.y, b.y * d.x));
+  }
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
 };
 template <typename R> struct PsiAccOf { using T = Acc64; };
 template <> struct PsiAccOf<float> { using T = Acc32x2; };
 
+template <typename A>
+__device__ __forceinline__ typename PsiOf<double>::T psi_out(const A &a, double r2) { return a.times(r2); }
+__device__ __forceinline__ float2 psi_out(const Acc32x2 &a, double r2) {
+  const float r2h = (float)r2, r2l = (float)(r2 - (double)r2h);
+  return a.times2(r2h, r2l);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   using A = typename PsiAccOf<R>::T;
+  using T = typename A::Term;
+  using P = typename PsiOf<R>::T;
   extern __shared__ __align__(16) unsigned char psmem[];
-  R *row = reinterpret_cast<R *>(psmem);  // nt + 1 values
+  T *row = reinterpret_cast<T *>(psmem);  // nt + 1 terms
   __shared__ A warp_tot[kPsiThreads / 32];
   const int i = blockIdx.x, nt = p.nt, tid = threadIdx.x;
   const R *br = p.f.br + (int64_t)i * nt;
   const R *br0 = p.f.br0 + (int64_t)i * nt;
-  for (int j = tid; j < nt; j += kPsiThreads) row[psi_pad(j)] = (br0[j] + br[j]) * (R)p.t.dcp[j];
+  for (int j = tid; j < nt; j += kPsiThreads) row[psi_pad(j)] = A::term(p, br0[j], br[j], j);
   __syncthreads();
   const int chunk = (nt + kPsiThreads - 1) / kPsiThreads;
   const int j0 = min(tid * chunk, nt), j1 = min(j0 + chunk, nt);
@@ -96,16 +127,16 @@ __global__ void __launch_bounds__(kPsiThreads) k_psi(Params<R> p) {
   run.add(acc.neg());
   for (int w = 0; w < wid; ++w) run.add(warp_tot[w]);
   const double r2 = p.t.r2n[i];
-  // rewrite the chunk in place with the prefix (inclusive, shifted by one)
-  R prev = (j0 < j1) ? row[psi_pad(j0)] : R(0);
+  // rewrite the chunk in place with the prefix (inclusive, shifted by one;
+  // a term and a Psi value have the same type), then store the row coalesced
+  static_assert(sizeof(T) == sizeof(P), "term and Psi share the staged row");
   for (int j = j0; j < j1; ++j) {
-    run.add(prev);
-    prev = (j + 1 < j1) ? row[psi_pad(j + 1)] : R(0);
-    row[psi_pad(j)] = (R)run.times(r2);  // becomes Psi(i, j+1)
+    run.add(row[psi_pad(j)]);
+    row[psi_pad(j)] = psi_out(run, r2);  // becomes Psi(i, j+1)
   }
   __syncthreads();
-  R *psi = p.f.psi + (int64_t)i * (nt + 1);
-  for (int j = tid; j <= nt; j += kPsiThreads) psi[j] = (j == 0) ? R(0) : row[psi_pad(j - 1)];
+  P *psi = p.f.psi + (int64_t)i * (nt + 1);
+  for (int j = tid; j <= nt; j += kPsiThreads) psi[j] = (j == 0) ? P{} : row[psi_pad(j - 1)];
 }
 
 // ----------------------------------------------------------- collocation
@@ -141,11 +172,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_a(Params<R> p) {
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   const Fields<R> &f = p.f;
-  if (i < nr && j < nt) {
-    const R pc = R(0.25) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)] + f.psi[ix(i, j + 1, n1)] +
-                            f.psi[ix(i + 1, j + 1, n1)]);
-    f.ffcell[ix(i, j, nt)] = (blend(p, pc) >= R(1)) ? 1 : 0;
-  }
+  if (i < nr && j < nt) f.ffcell[ix(i, j, nt)] = ff_cell(p, i, j) ? 1 : 0;
   R jx = 0, jy = 0, jz = 0;
   if (i >= 1 && i < nr) {
     R e[3], b[3];
@@ -233,7 +260,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
     if (j < nt) c += t.sh[j] * f.bp[ix(i, j, nt)];
     if (j > 0) c -= t.sh[j - 1] * f.bp[ix(i, j - 1, nt)];
     c *= t.inv_rh[i] * t.inv_dch[j];
-    const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
+    const R fb = blend_redge(p, i, j);
     const int64_t k = ix(i, j, n1);
     const R jt = (R(1) - fb) * f.jr[k] + fb * edge_r_mean(f.jpr, i, j, nr, n1);
     f.er[k] = (f.er[k] + dt * (c + f.sr[k]) - fp * jt) * (R(1) - t.sig_h[i]);
@@ -248,7 +275,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
       v = R(0);
     } else {
       const R c = -t.c_e2[i] * (t.rh[i] * f.bp[ix(i, j, nt)] - t.rh[i - 1] * f.bp[ix(i - 1, j, nt)]);
-      const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
+      const R fb = blend_tedge(p, i, j);
       const R jt = (R(1) - fb) * f.jt[k] + fb * R(0.5) * (f.jpt[ix(i, j, n1)] + f.jpt[ix(i, j + 1, n1)]);
       v = (f.et[k] + dt * (c + f.st[k]) - fp * jt) * (R(1) - t.sig_n[i]);
     }
@@ -261,7 +288,7 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
     if (i >= 1 && i < nr && j >= 1 && j < nt) {
       const R c = t.c_e2[i] * (t.rh[i] * f.bt[ix(i, j, n1)] - t.rh[i - 1] * f.bt[ix(i - 1, j, n1)]) -
                   t.c_ep2[i] * (f.br[ix(i, j, nt)] - f.br[ix(i, j - 1, nt)]);
-      const R fb = blend(p, f.psi[k]);
+      const R fb = blend_node(p, i, j);
       const R jt = (R(1) - fb) * f.jp[k] + fb * f.jpp[k];
       v = (f.ep[k] + dt * (c + f.sp[k]) - fp * jt) * (R(1) - t.sig_n[i]);
     }
@@ -318,7 +345,7 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   const Fields<R> &f = p.f;
   const bool lit = p.ff_interp_e != 0;
   if (i < nr) {
-    const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i + 1, j, n1)]));
+    const R fb = blend_redge(p, i, j);
     if (fb != R(0)) {
       const int64_t k = ix(i, j, n1);
       const R m = edge_r_mean(f.der, i, j, nr, n1);
@@ -327,7 +354,7 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   }
   if (i >= 1 && i < nr) {
     if (j < nt) {
-      const R fb = blend(p, R(0.5) * (f.psi[ix(i, j, n1)] + f.psi[ix(i, j + 1, n1)]));
+      const R fb = blend_tedge(p, i, j);
       if (fb != R(0)) {
         const int64_t k = ix(i, j, nt);
         const R m = R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]);
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
       }
     }
     if (j >= 1 && j < nt) {
-      const R fb = blend(p, f.psi[ix(i, j, n1)]);
+      const R fb = blend_node(p, i, j);
       if (fb != R(0)) {
         const int64_t k = ix(i, j, n1);
         const R m = f.dep[k];
@@ -345,9 +372,23 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   }
 }
 
+// The blend weights of the last flux prefix, on request (hff_fields): f at
+// the E_r and E_th edges and at the nodes, and the force-free cell flags
+// (outputs passed as null are skipped).
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_blend_out(Params<R> p, R *fr, R *ft, R *fn, uint8_t *cells) {
+  const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  if (j > nt) return;
+  if (fr && i < nr) fr[ix(i, j, n1)] = blend_redge(p, i, j);
+  if (ft && j < nt) ft[ix(i, j, nt)] = blend_tedge(p, i, j);
+  if (fn) fn[ix(i, j, n1)] = blend_node(p, i, j);
+  if (cells && i < nr && j < nt) cells[ix(i, j, nt)] = ff_cell(p, i, j) ? 1 : 0;
+}
+
 static inline dim3 row_grid(int rows, int nt) { return dim3((nt + 1 + kRowThreads - 1) / kRowThreads, rows); }
 
-template <typename R> size_t psi_smem(int nt) { return (size_t)(psi_pad(nt) + 2) * sizeof(R); }
+template <typename R> size_t psi_smem(int nt) { return (size_t)(psi_pad(nt) + 2) * 8; }
 template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s) {
   const size_t smem = psi_smem<R>(p.nt);
   k_psi<R><<<p.nr + 1, kPsiThreads, smem, s>>>(p);
@@ -366,6 +407,10 @@ template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s) {
 template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s) {
   k_node_b<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
   k_correct<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+}
+
+template <typename R> void launch_blend_out(const Params<R> &p, R *fr, R *ft, R *fn, uint8_t *cells, cudaStream_t s) {
+  k_blend_out<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p, fr, ft, fn, cells);
 }
 
 template <typename R>
@@ -387,7 +432,8 @@ template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
-  template void launch_correct<R>(const Params<R> &, cudaStream_t);
+  template void launch_correct<R>(const Params<R> &, cudaStream_t);            \
+  template void launch_blend_out<R>(const Params<R> &, R *, R *, R *, uint8_t *, cudaStream_t);
 HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST

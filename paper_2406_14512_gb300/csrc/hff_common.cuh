@@ -39,6 +39,46 @@ constexpr unsigned kStWorklist = 4u;
 constexpr unsigned kStNonfiniteField = 8u;
 constexpr unsigned kStBadCell = 16u;   // a loaded cell index outside the grid
 
+// Psi at the nodes (Eq. 27).  FP64 in FP64 instances.  In FP32 instances a
+// normalised pair of floats (value hi + lo with |lo| <= ulp(hi)/2, about 48
+// significant bits) summed from exact products of the FP32 B_r and the FP64
+// face factors, so that the blend decision against the breakpoints of
+// Eqs. 29-31 is taken at FP64-like resolution while all arithmetic runs on
+// the FP32 pipes (FP64 throughput on this GPU is a small fraction of FP32).
+template <typename R> struct PsiOf { using T = double; };
+template <> struct PsiOf<float> { using T = float2; };
+
+// exact sum of two floats as a (rounded sum, error) pair (Knuth's two-sum)
+__host__ __device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b, bv = s - a;
+  return make_float2(s, (a - (s - bv)) + (b - bv));
+}
+__host__ __device__ __forceinline__ float2 psi_add(float2 a, float2 b) {
+  const float2 s = two_sum(a.x, b.x);
+  const float e = s.y + (a.y + b.y);
+  const float h = s.x + e;  // |e| << |s.x|: fast renormalisation
+  return make_float2(h, e - (h - s.x));
+}
+__host__ __device__ __forceinline__ double psi_add(double a, double b) { return a + b; }
+// scaling by a power of two is exact
+__host__ __device__ __forceinline__ float2 psi_scale(float2 a, float k) { return make_float2(a.x * k, a.y * k); }
+__host__ __device__ __forceinline__ double psi_scale(double a, double k) { return a * k; }
+// order of normalised pairs: lexicographic (equal values have equal pairs)
+__host__ __device__ __forceinline__ bool psi_lt(float2 a, float2 b) { return a.x < b.x || (a.x == b.x && a.y < b.y); }
+__host__ __device__ __forceinline__ bool psi_lt(double a, double b) { return a < b; }
+__host__ __device__ __forceinline__ float psi_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+__host__ __device__ __forceinline__ double psi_diff(double a, double b) { return a - b; }
+// Psi at an edge is the mean of its two nodes, at a cell the mean of four
+template <typename P> __device__ __forceinline__ P psi_mean2(P a, P b) { return psi_scale(psi_add(a, b), 0.5f); }
+template <typename P> __device__ __forceinline__ P psi_mean4(P a, P b, P c, P d) {
+  return psi_scale(psi_add(psi_add(psi_add(a, b), c), d), 0.25f);
+}
+// a double as a normalised pair (about 48 bits kept)
+inline float2 psi_pair_of(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 template <typename R>
 struct Tables {
   // rows
@@ -67,6 +107,7 @@ struct Tables {
   const R *inv_dcp; // nt    1/(cos theta_j - cos theta_{j+1})
   const R *inv_dch; // nt+1  1/(cos theta_lo - cos theta_hi) of the node dual cell
   const double *dcp;  // nt    cos theta_j - cos theta_{j+1} (Psi prefix, FP64)
+  const float2 *dcp2; // nt    the same as a normalised float pair (FP32 prefix)
 };
 
 template <typename R>
@@ -76,7 +117,7 @@ struct Fields {
   R *br0, *bt0, *bp0;               // initial field B_0 (also the absorber reference)
   R *sr, *st, *sp;                  // curl B_0 at the E locations (computed in FP64)
   R *jr, *jt, *jp;                  // J_PIC accumulators (E locations)
-  R *psi;                           // Psi at nodes (FP64 prefix, rounded to R)
+  typename PsiOf<R>::T *psi;        // Psi at nodes (FP64, or a float pair)
   R *jpr, *jpt, *jpp;               // J_perp at nodes
   R *der, *det, *dep;               // Delta E at nodes
   uint8_t *ffcell;                  // 1 = cell in the pure force-free domain
@@ -96,8 +137,9 @@ struct Params {
   int small_grid;           // dlog and dtheta both below the series threshold
   uint32_t div_m, div_s1, div_s2;  // cell / nt by multiplication (see decode_cell)
   int n_breaks;
-  R psi_break[kMaxBreaks];  // absolute units
+  typename PsiOf<R>::T psi_bk[kMaxBreaks];  // breakpoints, absolute units
   R f_break[kMaxBreaks];
+  R f_slope[kMaxBreaks];    // (f_k - f_{k-1}) / (psi_k - psi_{k-1}); 0 at a jump
   int n_species;
   R q[kMaxSpecies], qm[kMaxSpecies], m[kMaxSpecies], krr[kMaxSpecies];
   Tables<R> t;
@@ -138,20 +180,41 @@ struct Params {
   R *ev_xo, *ev_yo, *ev_ur, *ev_ut, *ev_up, *ev_w;
 };
 
-// piecewise-linear blend f(Psi) of Eqs. 29-31 (right-continuous at jumps)
+// piecewise-linear blend f(Psi) of Eqs. 29-31 (right-continuous at jumps);
+// the segment is chosen by comparisons at the precision of Psi
 template <typename R>
-__device__ __forceinline__ R blend(const Params<R> &p, R psi) {
+__device__ __forceinline__ R blend(const Params<R> &p, typename PsiOf<R>::T psi) {
   const int n = p.n_breaks;
   if (n <= 0) return R(0);
-  if (psi < p.psi_break[0]) return p.f_break[0];
+  if (psi_lt(psi, p.psi_bk[0])) return p.f_break[0];
 #pragma unroll
-  for (int k = 1; k < kMaxBreaks; ++k) {
-    if (k < n && psi < p.psi_break[k]) {
-      const R x0 = p.psi_break[k - 1], x1 = p.psi_break[k];
-      return p.f_break[k - 1] + (p.f_break[k] - p.f_break[k - 1]) * (psi - x0) / (x1 - x0);
-    }
-  }
+  for (int k = 1; k < kMaxBreaks; ++k)
+    if (k < n && psi_lt(psi, p.psi_bk[k]))
+      return p.f_break[k - 1] + p.f_slope[k] * (R)psi_diff(psi, p.psi_bk[k - 1]);
   return p.f_break[n - 1];
+}
+
+// f on the edges and nodes of the mesh, and the pure force-free flag of a
+// cell (f of its mean-corner Psi >= 1: no particles there, Eq. 29)
+template <typename R>
+__device__ __forceinline__ R blend_redge(const Params<R> &p, int i, int j) {  // E_r(i+1/2, j)
+  const int n1 = p.nt + 1;
+  return blend(p, psi_mean2(p.f.psi[(int64_t)i * n1 + j], p.f.psi[(int64_t)(i + 1) * n1 + j]));
+}
+template <typename R>
+__device__ __forceinline__ R blend_tedge(const Params<R> &p, int i, int j) {  // E_th(i, j+1/2)
+  const int64_t k = (int64_t)i * (p.nt + 1) + j;
+  return blend(p, psi_mean2(p.f.psi[k], p.f.psi[k + 1]));
+}
+template <typename R>
+__device__ __forceinline__ R blend_node(const Params<R> &p, int i, int j) {  // E_ph(i, j)
+  return blend(p, p.f.psi[(int64_t)i * (p.nt + 1) + j]);
+}
+template <typename R>
+__device__ __forceinline__ bool ff_cell(const Params<R> &p, int i, int j) {
+  const int n1 = p.nt + 1;
+  const int64_t k = (int64_t)i * n1 + j;
+  return blend(p, psi_mean4(p.f.psi[k], p.f.psi[k + n1], p.f.psi[k + 1], p.f.psi[k + n1 + 1])) >= R(1);
 }
 
 // cell = i * nt + j  ->  (i, j) with the division by the invariant nt done
@@ -176,6 +239,9 @@ template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s);
 template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
+// f at the E_r edges, E_th edges and nodes, and the force-free cell flags,
+// from the current Psi (on request)
+template <typename R> void launch_blend_out(const Params<R> &p, R *fr, R *ft, R *fn, uint8_t *cells, cudaStream_t s);
 // dst[k] = a[k] + sign * b[k], k < n (B <-> B - B_0 at the ABI)
 template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_t n, int sign, cudaStream_t s);
 

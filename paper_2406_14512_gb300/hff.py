@@ -34,7 +34,8 @@ HOST, DEVICE = 0, 1
 ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255)
 SCALAR_RR_SCALE = 0
 FIELDS = ["E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph", "J_r", "J_th", "J_ph", "psi",
-          "jperp_r", "jperp_th", "jperp_ph", "dE_r", "dE_th", "dE_ph"]
+          "jperp_r", "jperp_th", "jperp_ph", "dE_r", "dE_th", "dE_ph",
+          "f_r", "f_th", "f_node", "ff_cell"]
 
 
 class HffError(RuntimeError):
@@ -321,10 +322,13 @@ class _InstanceOps:
     def shape(self, name: str):
         nr, nt = self.nr, self.nt
         return {"E_r": (nr, nt + 1), "J_r": (nr, nt + 1), "E_th": (nr + 1, nt), "J_th": (nr + 1, nt),
-                "B_r": (nr + 1, nt), "B_th": (nr, nt + 1), "B_ph": (nr, nt)}.get(name, (nr + 1, nt + 1))
+                "B_r": (nr + 1, nt), "B_th": (nr, nt + 1), "B_ph": (nr, nt), "f_r": (nr, nt + 1),
+                "f_th": (nr + 1, nt), "ff_cell": (nr, nt)}.get(name, (nr + 1, nt + 1))
 
     def get(self, name: str) -> np.ndarray:
-        dt = np.float64 if name == "psi" else self.real
+        """A field, J, Psi (FP64), a node array, or the blend weights f_r, f_th,
+        f_node and the force-free cell flags ff_cell (uint8) of the current B."""
+        dt = np.float64 if name == "psi" else (np.uint8 if name == "ff_cell" else self.real)
         out = np.empty(self.shape(name), dt)
         hff_fields(self.h, self.inst, FIELDS.index(name), out.ctypes.data, out.nbytes, HOST)
         return out
