@@ -89,6 +89,7 @@ def lib():
         L.or_psi_unit.argtypes = [vp]
         L.or_step_index.restype = i64
         L.or_step_index.argtypes = [vp]
+        L.or_set_step_index.argtypes = [vp, i64]
         L.or_field_size.restype = i64
         L.or_field_size.argtypes = [vp, C.c_int]
         L.or_get_field.argtypes = [vp, C.c_int, vp]
@@ -191,6 +192,10 @@ class Oracle:
     @property
     def step_index(self) -> int:
         return self.L.or_step_index(self.h)
+
+    @step_index.setter
+    def step_index(self, v: int) -> None:
+        self.L.or_set_step_index(self.h, int(v))
 
     def shape(self, name: str):
         nr, nt = self.nr, self.nt

@@ -339,6 +339,10 @@ void or_destroy(void *st) {
 double or_dt(void *st) { return ((ost *)st)->dt; }
 double or_psi_unit(void *st) { return ((ost *)st)->psi_unit; }
 int64_t or_step_index(void *st) { return ((ost *)st)->step; }
+/* Sets the step counter (the injection generator's key and the sort cadence);
+ * a caller that splits one step into several stage groups uses it so that the
+ * step counts once (tests only). */
+void or_set_step_index(void *st, int64_t step) { ((ost *)st)->step = step; }
 int64_t or_field_size(void *st, int which) { return fsize((ost *)st, which); }
 int or_get_field(void *st, int which, double *out) {
   ost *s = (ost *)st;

@@ -110,6 +110,7 @@ void or_destroy(void *st);
 double or_dt(void *st);
 double or_psi_unit(void *st);
 int64_t or_step_index(void *st);
+void or_set_step_index(void *st, int64_t step); /* one step split into stage groups */
 
 /* which: 0..5 = E_r E_th E_ph B_r B_th B_ph; 6..8 = J_r J_th J_ph (PIC);
  *        9 = psi (nodes); 10..12 = J_perp at nodes; 13..15 = Delta E at nodes;
