@@ -154,6 +154,19 @@ typedef struct hff_config {
                                solution, but it lets a mode grow near the axis
                                next to a force-free / PIC interface within
                                ~1e4-1e5 steps on 1024^2 - 2048^2 grids)          */
+  double ff_filter;         /* sigma in [0, 1] of a fourth-difference filter of
+                               E_r along r and E_th along theta, applied with the
+                               correction, weighted by f: E -= f sigma/16 D4(E).
+                               The two-point means of the collocation do not see
+                               the odd-even component of those fields, so the
+                               node corrections cannot act on it; sigma = 1
+                               removes it, and a smooth field changes by O(h^4)
+                               per step.  0 = off (a reading: the paper is silent) */
+  int32_t ff_return_every;  /* with ff_delta_only = 1: on the steps whose index
+                               (the step counter before the step) is a multiple
+                               of this value (> 0) the corrected field itself
+                               returns, as with ff_delta_only = 0; the
+                               corrections alone on the others (0 = never)       */
 } hff_config;
 
 typedef struct hff_info {
@@ -252,9 +265,10 @@ int hff_fields(hff_handle *h, int inst, int which, void *dst, size_t bytes, int 
 int hff_step(hff_handle *h, int32_t nsteps);
 
 /* As hff_step, but for step k records the caller's CUDA events ev_begin[k]
- * and ev_end[k] (cudaEvent_t) on the stream immediately before and after the
- * tile-staged push kernel, so that its duration can be timed inside a run of
- * whole steps.  The step then runs as three graph launches instead of one. */
+ * and ev_end[k] (cudaEvent_t) immediately before and after the tile-staged
+ * push kernel, so that its duration can be timed inside a run of whole
+ * steps.  The step is the same single graph as hff_step's with two event-
+ * record nodes added, whose events are set before each launch. */
 int hff_step_timed(hff_handle *h, int32_t nsteps, void *const *ev_begin, void *const *ev_end);
 
 /* Advance nsteps steps running only the stages in the HFF_ST_* mask (eager

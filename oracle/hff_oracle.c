@@ -453,8 +453,9 @@ static void node_pass_b(ost *s) {
       for (int k = 0; k < 3; ++k) NODE(13 + k, i, j) = sc * ep[k] - e[k];
     }
   /* reading "interpolate these back" literally: the corrected node field
-   * E'' = E + Delta E itself returns to the edges                         */
-  if (!s->c.ff_delta_only)
+   * E'' = E + Delta E itself returns to the edges (every step, or on the
+   * steps of ff_return_every)                                              */
+  if (!s->c.ff_delta_only || (s->c.ff_return_every > 0 && s->step % s->c.ff_return_every == 0))
     for (int i = 1; i < nr; ++i)
       for (int j = 0; j <= nt; ++j) {
         double e[3], b[3];
@@ -478,23 +479,57 @@ static double edge_r_mean(const ost *s, int k, int i, int j) {
  * arithmetic means (Sect. 3) and applied with the blend weight f(Psi^n) of
  * Eqs. 29-31: full in the force-free domain, absent in pure PIC, linear
  * across the layer.  Psi on an edge is the mean of its nodes.               */
+/* Fourth differences of E_r along r and of E_th along theta at the edges
+ * (zero where the five-point stencil does not fit), from the field as it is
+ * before the correction.  The two-point means of the collocation (Sect. 3)
+ * do not see the odd-even component of E_r along r or of E_th along theta,
+ * so the node corrections cannot act on it; the filter E -= f sigma/16 D4 E
+ * (reading, optional) removes that component (sigma = 1) and changes a
+ * smooth field by O(h^4) per step.                                          */
+static double d4_er(const ost *s, int i, int j) {
+  if (i < 2 || i > s->nr - 3) return 0.0;
+  return ER(i - 2, j) - 4 * ER(i - 1, j) + 6 * ER(i, j) - 4 * ER(i + 1, j) + ER(i + 2, j);
+}
+static double d4_et(const ost *s, int i, int j) {
+  if (j < 2 || j > s->nt - 3) return 0.0;
+  return ET(i, j - 2) - 4 * ET(i, j - 1) + 6 * ET(i, j) - 4 * ET(i, j + 1) + ET(i, j + 2);
+}
+
 static void correct_e(ost *s) {
   int nr = s->nr, nt = s->nt, lit = s->c.ff_delta_only == 0;
+  /* reading: the corrected field itself may return once every
+   * ff_return_every steps, the corrections alone in between               */
+  if (!lit && s->c.ff_return_every > 0 && s->step % s->c.ff_return_every == 0) lit = 1;
+  double sg = s->c.ff_filter / 16.0;
+  double *fr = NULL, *ft = NULL;
+  if (sg != 0.0) { /* the filter terms from the uncorrected E */
+    fr = (double *)calloc(fsize(s, 0), sizeof(double));
+    ft = (double *)calloc(fsize(s, 1), sizeof(double));
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j <= nt; ++j) fr[(int64_t)i * (nt + 1) + j] = sg * d4_er(s, i, j);
+    for (int i = 1; i < nr; ++i)
+      for (int j = 0; j < nt; ++j) ft[(int64_t)i * nt + j] = sg * d4_et(s, i, j);
+  }
   node_pass_b(s);
   /* with the literal reading the edge value moves toward the mean of the
-   * corrected node fields, E <- E + f (<E''> - E); otherwise E += f <dE>   */
+   * corrected node fields, E <- E + f (<E''> - E); otherwise E += f <dE>;
+   * the optional filter term is subtracted with the same weight f         */
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j <= nt; ++j) {
       double f = blend(s, 0.5 * (PSI(i, j) + PSI(i + 1, j)));
       double m = edge_r_mean(s, 13, i, j);
+      if (fr) m -= fr[(int64_t)i * (nt + 1) + j];
       if (f != 0.0) ER(i, j) += f * (lit ? m - ER(i, j) : m);
     }
   for (int i = 1; i < nr; ++i)
     for (int j = 0; j < nt; ++j) {
       double f = blend(s, 0.5 * (PSI(i, j) + PSI(i, j + 1)));
       double m = 0.5 * (NODE(14, i, j) + NODE(14, i, j + 1));
+      if (ft) m -= ft[(int64_t)i * nt + j];
       if (f != 0.0) ET(i, j) += f * (lit ? m - ET(i, j) : m);
     }
+  free(fr);
+  free(ft);
   for (int i = 1; i < nr; ++i)
     for (int j = 1; j < nt; ++j) {
       double f = blend(s, PSI(i, j));

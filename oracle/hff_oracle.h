@@ -81,6 +81,12 @@ typedef struct or_config {
   int32_t inject_species[2]; /* species injected together; equal = (0, 1)   */
   int32_t ff_delta_only;     /* 0: the corrected node E returns to the edges,
                                 1: only the corrections Delta E (Sect. 3)   */
+  double ff_filter;          /* sigma of the fourth-difference filter of E_r
+                                along r and E_th along theta where f > 0
+                                (0 = off; 1 removes the odd-even mode)      */
+  int32_t ff_return_every;   /* with ff_delta_only = 1: on steps whose index
+                                is a multiple of this (> 0) the corrected
+                                field itself returns (0 = never)            */
 } or_config;
 
 typedef struct or_diag {

@@ -121,6 +121,8 @@ int validate(const hff_config *c) {
   if (!(c->gamma_th == 0 || c->gamma_th > 1) || (c->gamma_th > 0 && !(c->gamma_s >= 1.0)))
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
+  if (!(c->ff_filter >= 0.0 && c->ff_filter <= 1.0)) return fail(HFF_ERR_ARG, "ff_filter must be in [0, 1]");
+  if (c->ff_return_every < 0) return fail(HFF_ERR_ARG, "ff_return_every must be >= 0");
   if (c->inject_species[0] != c->inject_species[1])
     for (int k = 0; k < 2; ++k)
       if (c->inject_species[k] < 0 || c->inject_species[k] >= c->n_species)
@@ -261,8 +263,13 @@ struct hff_handle {
   // graphs are cached per [buffer parity][pending]
   bool pending = false;
   cudaGraphExec_t g_step[2][2] = {}, g_sort[2] = {nullptr, nullptr};
-  cudaGraphExec_t g_part[2][2][3] = {};
-  int64_t k_step[2][2] = {}, k_sort[2] = {0, 0}, k_part[2][2][3] = {};
+  // the timed step: the same graph as g_step plus two external event-record
+  // nodes around the tiled push, whose events are set per launch
+  cudaGraphExec_t g_timed[2][2] = {};
+  cudaGraph_t gg_timed[2][2] = {};
+  cudaGraphNode_t n_evb[2][2] = {}, n_eve[2][2] = {};
+  cudaEvent_t ev_ph[2] = {nullptr, nullptr};
+  int64_t k_step[2][2] = {}, k_sort[2] = {0, 0}, k_timed[2][2] = {};
   int64_t launched = 0;
   // pinned host staging: per-step scalars (a ring, so queued copies never
   // see a later value) and the counter readback
@@ -377,6 +384,8 @@ void fill_params(hff_handle *h) {
     p.inj_sp[0] = dflt ? 0 : c.inject_species[0];
     p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
     p.ff_interp_e = c.ff_delta_only ? 0 : 1;
+    p.ff_sigma16 = (R)(c.ff_filter / 16.0);
+    p.ff_return_every = c.ff_delta_only ? c.ff_return_every : 0;
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
     p.pushed = h->small->pushed;
@@ -710,24 +719,68 @@ int do_step(hff_handle *h, int32_t n) {
   return HFF_OK;
 }
 
+// The timed step graph: the kernels of g_step with an external event-record
+// node before and after the tiled push (placeholder events at capture; the
+// caller's events are set into the instantiated graph before each launch).
+template <typename R>
+int capture_timed(hff_handle *h, int par, int gz) {
+  for (int e = 0; e < 2; ++e)
+    if (!h->ev_ph[e]) CK(cudaEventCreateWithFlags(&h->ev_ph[e], cudaEventDisableTiming));
+  CK(cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step<R>(h, par, HFF_ST_ALL, h->cap_st, 1, gz != 0);
+  if (rc == HFF_OK && cudaEventRecordWithFlags(h->ev_ph[0], h->cap_st, cudaEventRecordExternal) != cudaSuccess)
+    rc = fail(HFF_ERR_CUDA, "event record node");
+  if (rc == HFF_OK) rc = enqueue_step<R>(h, par, HFF_ST_ALL, h->cap_st, 2, gz != 0);
+  if (rc == HFF_OK && cudaEventRecordWithFlags(h->ev_ph[1], h->cap_st, cudaEventRecordExternal) != cudaSuccess)
+    rc = fail(HFF_ERR_CUDA, "event record node");
+  if (rc == HFF_OK) rc = enqueue_step<R>(h, par, HFF_ST_ALL, h->cap_st, 4, gz != 0);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_st, &g);
+  if (rc != HFF_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return fail(HFF_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  for (auto &x : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(x, &t));
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev = nullptr;
+    CK(cudaGraphEventRecordNodeGetEvent(x, &ev));
+    if (ev == h->ev_ph[0]) h->n_evb[par][gz] = x;
+    if (ev == h->ev_ph[1]) h->n_eve[par][gz] = x;
+  }
+  int64_t nk = 0;
+  rc = count_kernels(g, &nk);
+  if (rc != HFF_OK || !h->n_evb[par][gz] || !h->n_eve[par][gz]) {
+    cudaGraphDestroy(g);
+    return rc != HFF_OK ? rc : fail(HFF_ERR_CUDA, "event nodes not found in the timed graph");
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&h->g_timed[par][gz], g, 0);
+  if (e2 != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(HFF_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e2));
+  }
+  h->gg_timed[par][gz] = g;  // kept: its node handles address the instantiated graph
+  h->k_timed[par][gz] = nk;
+  return HFF_OK;
+}
+
 template <typename R>
 int do_step_timed(hff_handle *h, int32_t n, void *const *evb, void *const *eve) {
   for (int32_t k = 0; k < n; ++k) {
     const int par = h->parity, gz = h->pending ? 1 : 0;
-    for (int part = 0; part < 3; ++part) {
-      if (!h->g_part[par][gz][part]) {
-        const int mask = 1 << part;
-        int rc = capture(h, [&](cudaStream_t s) { return enqueue_step<R>(h, par, HFF_ST_ALL, s, mask, gz != 0); },
-                         &h->g_part[par][gz][part], &h->k_part[par][gz][part]);
-        if (rc != HFF_OK) return rc;
-      }
+    if (!h->g_timed[par][gz]) {
+      const int rc = capture_timed<R>(h, par, gz);
+      if (rc != HFF_OK) return rc;
     }
-    CK(cudaGraphLaunch(h->g_part[par][gz][0], h->st));
-    if (evb && evb[k]) CK(cudaEventRecord((cudaEvent_t)evb[k], h->st));
-    CK(cudaGraphLaunch(h->g_part[par][gz][1], h->st));
-    if (eve && eve[k]) CK(cudaEventRecord((cudaEvent_t)eve[k], h->st));
-    CK(cudaGraphLaunch(h->g_part[par][gz][2], h->st));
-    h->launched += h->k_part[par][gz][0] + h->k_part[par][gz][1] + h->k_part[par][gz][2];
+    cudaEvent_t b = (evb && evb[k]) ? (cudaEvent_t)evb[k] : h->ev_ph[0];
+    cudaEvent_t e = (eve && eve[k]) ? (cudaEvent_t)eve[k] : h->ev_ph[1];
+    CK(cudaGraphExecEventRecordNodeSetEvent(h->g_timed[par][gz], h->n_evb[par][gz], b));
+    CK(cudaGraphExecEventRecordNodeSetEvent(h->g_timed[par][gz], h->n_eve[par][gz], e));
+    CK(cudaGraphLaunch(h->g_timed[par][gz], h->st));
+    h->launched += h->k_timed[par][gz];
     h->pending = false;
     h->step++;
     if (h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
@@ -862,10 +915,12 @@ void destroy_handle(hff_handle *h) {
     if (h->g_sort[p]) cudaGraphExecDestroy(h->g_sort[p]);
     for (int g = 0; g < 2; ++g) {
       if (h->g_step[p][g]) cudaGraphExecDestroy(h->g_step[p][g]);
-      for (int k = 0; k < 3; ++k)
-        if (h->g_part[p][g][k]) cudaGraphExecDestroy(h->g_part[p][g][k]);
+      if (h->g_timed[p][g]) cudaGraphExecDestroy(h->g_timed[p][g]);
+      if (h->gg_timed[p][g]) cudaGraphDestroy(h->gg_timed[p][g]);
     }
   }
+  for (int e = 0; e < 2; ++e)
+    if (h->ev_ph[e]) cudaEventDestroy(h->ev_ph[e]);
   for (hff_handle *m : h->members) destroy_handle(m);
   for (cudaStream_t f : h->fork) cudaStreamDestroy(f);
   for (cudaEvent_t ev : h->join) cudaEventDestroy(ev);
@@ -1467,7 +1522,8 @@ static bool same_run(const hff_config &a, const hff_config &b) {
             a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
             a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s &&
             a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1] &&
-            (a.ff_delta_only != 0) == (b.ff_delta_only != 0);
+            (a.ff_delta_only != 0) == (b.ff_delta_only != 0) && a.ff_filter == b.ff_filter &&
+            a.ff_return_every == b.ff_return_every;
   for (int k = 0; k < 4; ++k)
     eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
   return eq;

@@ -297,16 +297,41 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
   }
 }
 
+// The corrected field itself returns on this step: always with ff_interp_e,
+// else on the steps (device counter before the step) that ff_return_every
+// divides.
+template <typename R>
+__device__ __forceinline__ bool literal_step(const Params<R> &p) {
+  return p.ff_return_every > 0 && (*p.step % p.ff_return_every) == 0;
+}
+
 // ----------------------------------------------------------- node pass B
 // Renormalisation at interior nodes from E^{n+1} and B^{n+1/2}:
 // E' = E - (E.B) B/B^2 (Eq. 25), E'' = sqrt(B^2/E'^2) E' if E'^2 > B^2 (Eq. 26).
 // Stores Delta E = E'' - E, or E'' itself when the corrected field returns to
-// the edges (ff_interp_e).
+// the edges (ff_interp_e).  With the optional fourth-difference filter it also
+// stores sigma/16 D4 E_r (along r) at the E_r edge (i+1/2, j) and sigma/16
+// D4 E_th (along theta) at the E_th edge (i, j+1/2), from the same
+// uncorrected E, in the J_PIC arrays: those are zero between Ampere's law and
+// the next deposit, and the correction reads and clears them.
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
+  if (p.ff_sigma16 != R(0)) {
+    const Fields<R> &f = p.f;
+    if (i >= 2 && i <= nr - 3) {
+      const R d4 = f.er[ix(i - 2, j, n1)] - R(4) * f.er[ix(i - 1, j, n1)] + R(6) * f.er[ix(i, j, n1)] -
+                   R(4) * f.er[ix(i + 1, j, n1)] + f.er[ix(i + 2, j, n1)];
+      f.jr[ix(i, j, n1)] = p.ff_sigma16 * d4;
+    }
+    if (i >= 1 && i <= nr - 1 && j >= 2 && j <= nt - 3) {
+      const R d4 = f.et[ix(i, j - 2, nt)] - R(4) * f.et[ix(i, j - 1, nt)] + R(6) * f.et[ix(i, j, nt)] -
+                   R(4) * f.et[ix(i, j + 1, nt)] + f.et[ix(i, j + 2, nt)];
+      f.jt[ix(i, j, nt)] = p.ff_sigma16 * d4;
+    }
+  }
   R d0 = 0, d1 = 0, d2 = 0;
   bool clamped = false;
   if (i >= 1 && i < nr) {
@@ -323,7 +348,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
       d2 = sc * z - e[2];
       clamped = e2 > b2;
     }
-    if (p.ff_interp_e) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
+    if (p.ff_interp_e || literal_step(p)) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
   }
   // running count of Eq. 26 activations (failure detection: a force-free
   // region that keeps needing the clamp is going unstable)
@@ -337,27 +362,34 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
 // Delta E interpolated back to the staggered mesh by arithmetic means and
 // applied with the blend weight f (Sect. 3, Eqs. 29-31); or, with
 // ff_interp_e, the corrected node field itself: E <- E + f (<E''> - E).
+// The optional filter term (node pass B, in the J_PIC arrays) is subtracted
+// with the same weight and its slot cleared for the next deposit.
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   const Fields<R> &f = p.f;
-  const bool lit = p.ff_interp_e != 0;
+  const bool lit = p.ff_interp_e != 0 || literal_step(p);
+  const bool filt = p.ff_sigma16 != R(0);
   if (i < nr) {
+    const int64_t k = ix(i, j, n1);
     const R fb = blend_redge(p, i, j);
+    R g = R(0);
+    if (filt) { g = f.jr[k]; f.jr[k] = R(0); }
     if (fb != R(0)) {
-      const int64_t k = ix(i, j, n1);
-      const R m = edge_r_mean(f.der, i, j, nr, n1);
+      const R m = edge_r_mean(f.der, i, j, nr, n1) - g;
       f.er[k] += fb * (lit ? m - f.er[k] : m);
     }
   }
   if (i >= 1 && i < nr) {
     if (j < nt) {
+      const int64_t k = ix(i, j, nt);
       const R fb = blend_tedge(p, i, j);
+      R g = R(0);
+      if (filt) { g = f.jt[k]; f.jt[k] = R(0); }
       if (fb != R(0)) {
-        const int64_t k = ix(i, j, nt);
-        const R m = R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]);
+        const R m = R(0.5) * (f.det[ix(i, j, n1)] + f.det[ix(i, j + 1, n1)]) - g;
         f.et[k] += fb * (lit ? m - f.et[k] : m);
       }
     }

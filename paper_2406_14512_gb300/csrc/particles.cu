@@ -113,10 +113,27 @@ template <typename R> __device__ __forceinline__ R log1p_small(R x) {
 template <typename R> __device__ __forceinline__ R exp_small(R x) {
   return R(1) + x * (R(1) + x * R(0.5) * (R(1) + x * R(1.0 / 3.0) * (R(1) + x * R(0.25) * (R(1) + x * R(0.2) * (R(1) + x * R(1.0 / 6.0))))));
 }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// FP32 reciprocal, reciprocal square root and division as the single
+// approximate hardware instructions (about 1-2 ulp, denormals flushed): their
+// arguments here are squared norms, radii and ratios of per-step increments,
+// never denormal, and the results enter quantities compared with the FP64
+// oracle at 1e-5 relative
+__device__ __forceinline__ float rsq(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float fdiv(float a, float b) {
+  float y;
+  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(y) : "f"(a), "f"(b));
+  return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
@@ -261,7 +278,7 @@ __device__ __forceinline__ bool move_small(R r, R sn, R cs, R dt, const R u[3], 
   if (!(x > R(0)) || fabs(d2) >= R(kSmall) * x) return false;
   const R tp = fdiv(d2, x), qp = tp * tp;
   const R cp = rsq(R(1) + qp), sqp = (R(1) + qp) * cp;
-  const R sp = tp * cp, omc = qp / (sqp * (sqp + R(1)));  // 1 - cos(phi)
+  const R sp = tp * cp, omc = fdiv(qp, sqp * (sqp + R(1)));  // 1 - cos(phi)
   const R dR = x * omc * sqp;                                // sqrt(x^2+d2^2) - x
   const R pa = d0 + dR * sn;
   const R a = r + pa, bb = d1 + dR * cs;

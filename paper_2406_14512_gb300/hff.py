@@ -58,7 +58,7 @@ class hff_config(C.Structure):
         ("capacity", C.c_int64), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
         ("sort_every", C.c_int32), ("precision", C.c_int32),
         ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
-        ("ff_delta_only", C.c_int32),
+        ("ff_delta_only", C.c_int32), ("ff_filter", C.c_double), ("ff_return_every", C.c_int32),
     ]
 
 
@@ -171,12 +171,19 @@ def config_struct(cfg: dict) -> hff_config:
     c.capacity = int(cfg.get("capacity", 0))
     c.tile_r, c.tile_t = int(cfg.get("tile_r", 16)), int(cfg.get("tile_t", 32))
     c.sort_every = int(cfg.get("sort_every", 0))
+    if c.tile_r == 0 and c.tile_t == 0 and c.sort_every == -1:
+        # a shape left to the autotuner and not resolved (Sim resolves it):
+        # the library gets the tuner's fallback shape
+        from .autotune import DEFAULT_SHAPE
+        c.tile_r, c.tile_t, c.sort_every = DEFAULT_SHAPE
     c.precision = FP64 if cfg.get("precision", "fp32") == "fp64" else FP32
     c.gamma_th = float(cfg.get("gamma_th", 0.0))
     c.gamma_s = float(cfg.get("gamma_s", 0.0))
     isp = list(cfg.get("inject_species", [0, 1]))
     c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
     c.ff_delta_only = int(cfg.get("ff_delta_only", 0))
+    c.ff_filter = float(cfg.get("ff_filter", 0.0))
+    c.ff_return_every = int(cfg.get("ff_return_every", 0))
     return c
 
 
@@ -440,10 +447,19 @@ def _device_and_stream(device, stream):
 
 
 class Sim(_InstanceOps, _Stepping):
-    """One instance in a torch-owned device buffer on the current stream."""
+    """One instance in a torch-owned device buffer on the current stream.
 
-    def __init__(self, cfg: dict, device: str = "cuda:0", stream=None):
+    A configuration with tile_r = tile_t = 0 and sort_every = -1 gets its
+    launch shape from the autotuner (autotune.resolve): measured on
+    `particles` (the species list the caller will load) and cached, or the
+    cached / default shape when no particles are given."""
+
+    def __init__(self, cfg: dict, device: str = "cuda:0", stream=None, particles=None):
         self.torch, self.dev, self.stream = _device_and_stream(device, stream)
+        from . import autotune
+        if autotune.wants_tuning(cfg):
+            with self.torch.cuda.device(self.dev):
+                cfg = autotune.resolve(cfg, particles)
         self.cfg = dict(cfg)
         self.c = config_struct(cfg)
         self.inst = 0

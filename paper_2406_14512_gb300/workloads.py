@@ -78,12 +78,12 @@ def config(name: str) -> dict:
         c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=150_000_000,
                  steps=1000, precision="fp32", place="band", sheet_frac=0.2, momenta="powerlaw")
         c["gamma_rad"] = 0.05 * (c["r_lc"] ** -2) / c["m"][0]  # 5% of gamma_pc = e Phi_pc / m c^2
-        c.update(tile_t=24, sort_every=12)  # launch shape chosen by autotune.py (16 x 24, every 12 steps)
+        c.update(tile_r=0, tile_t=0, sort_every=-1)  # launch shape measured by the autotuner at init
     elif name == "c4":
         c = _base(8192, 8192, 200.0, 20.0, "synth", kappa=1.0, seed=1237)
         c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=500_000_000,
                  steps=500, precision="fp32", place="band", sheet_frac=0.2, momenta="maxwell",
-                 tile_t=24, sort_every=12)
+                 tile_r=0, tile_t=0, sort_every=-1)  # launch shape measured by the autotuner at init
     elif name.startswith("small_"):
         # reduced-size parity variants, spanning several tiles and a ragged tail
         kind = name[len("small_"):]

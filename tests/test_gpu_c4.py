@@ -73,6 +73,7 @@ def test_c4_band_push_deposit(c4):
     hff, cfg, ps = c4
     nt = cfg["nt"]
     sim = hff.Sim(cfg)
+    cfg = sim.cfg  # the launch shape the autotuner resolved
     for s in range(2):
         sim.load(s, ps[s])
     lo, hi = 3560, 3576                 # rows near r = R_LC / 2 (dipole zone, PIC band)

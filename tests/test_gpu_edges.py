@@ -61,6 +61,36 @@ def test_cell_outside_the_grid_is_rejected_on_load(env):
         sim.close()
 
 
+def test_timed_step_is_the_production_step(env):
+    """hff_step_timed replays the production step graph with two event-record
+    nodes around the tiled push: the same result as hff_step (up to the order
+    of the atomic sums) and positive push durations inside each step."""
+    import torch
+    hff, workloads, _ = env
+    cfg = workloads.config("small_hybrid")
+    cfg.update(capacity=40000, sort_every=4)
+    ps = workloads.particles(cfg, n_pairs=5000, seed=8)
+    a, b = hff.Sim(cfg), hff.Sim(cfg)
+    for s in range(2):
+        a.load(s, ps[s])
+        b.load(s, ps[s])
+    a.step(9)
+    evb = [torch.cuda.Event(enable_timing=True) for _ in range(9)]
+    eve = [torch.cuda.Event(enable_timing=True) for _ in range(9)]
+    b.step_timed(evb, eve)
+    torch.cuda.synchronize()
+    for f in FIELDS6:
+        assert rel_l2(b.get(f), a.get(f)) < 1e-5, f
+    for s in range(2):
+        ca, cb = a.particles(s)["cell"], b.particles(s)["cell"]
+        assert len(ca) == len(cb) and np.mean(ca == cb) > 0.999
+    ms = [evb[k].elapsed_time(eve[k]) for k in range(9)]
+    assert all(m > 0 for m in ms)
+    assert a.info().kernels_launched == b.info().kernels_launched
+    a.close()
+    b.close()
+
+
 def test_capacity_overflow_is_latched(env):
     hff, workloads, _ = env
     cfg = workloads.config("small_pic")

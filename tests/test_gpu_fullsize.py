@@ -32,6 +32,7 @@ def full():
     cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
     ps = workloads.particles(cfg, threads=16)
     sim = hff.Sim(cfg)
+    cfg = sim.cfg  # the launch shape the autotuner resolved
     for s in range(2):
         sim.load(s, ps[s])
     return cfg, ps, sim

@@ -37,12 +37,16 @@ def make(env, name, **kw):
     return cfg, hff.Sim(cfg), oracle.Oracle(cfg)
 
 
-@pytest.mark.parametrize("name,prec,tol", [("small_hybrid", "fp32", 1e-5), ("small_rr", "fp32", 1e-5),
-                                           ("small_michel", "fp32", 1e-5), ("small_hybrid", "fp64", 1e-11)])
-def test_field_step_parity(env, name, prec, tol):
+@pytest.mark.parametrize("name,prec,tol,extra", [
+    ("small_hybrid", "fp32", 1e-5, {}), ("small_rr", "fp32", 1e-5, {}), ("small_michel", "fp32", 1e-5, {}),
+    ("small_hybrid", "fp64", 1e-11, {}),
+    # the corrections-only return with the fourth-difference filter of E_r, E_th
+    ("small_hybrid", "fp32", 1e-5, {"ff_delta_only": 1, "ff_filter": 1.0}),
+    ("small_michel", "fp64", 1e-11, {"ff_delta_only": 1, "ff_filter": 0.5})])
+def test_field_step_parity(env, name, prec, tol, extra):
     """Psi, J_perp, Yee advance, blended current, renormalisation, star and
     absorber: one field-only step from identical smooth fields."""
-    cfg, sim, ref = make(env, name, capacity=0, precision=prec, sort_every=0)
+    cfg, sim, ref = make(env, name, capacity=0, precision=prec, sort_every=0, **extra)
     shared_initial_state(sim, ref, seed=3)
     psi_g = sim.get("psi")  # FP64 prefix of the current B_r
     ref_psi = oracle_psi(ref)
@@ -53,6 +57,23 @@ def test_field_step_parity(env, name, prec, tol):
         assert rel_l2(sim.get(f), ref.get(f)) < tol, (f, rel_l2(sim.get(f), ref.get(f)))
     for f in ("jperp_r", "jperp_th", "jperp_ph"):
         assert rel_l2(sim.get(f), ref.get(f)) < 10 * tol, f
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_periodic_literal_return_parity(env, prec, tol):
+    """The corrections-only return with the corrected field itself returning
+    every third step (device step counter against the oracle's): five field
+    steps from the same fields, literal on steps 0 and 3."""
+    cfg, sim, ref = make(env, "small_michel", capacity=0, precision=prec, sort_every=0, ff_delta_only=1,
+                         ff_return_every=3)
+    shared_initial_state(sim, ref, seed=5)
+    sim.step_stages(5, FIELD_STAGES)
+    ref.step(5, FIELD_STAGES)
+    for f in ("B_r", "B_th", "B_ph", "E_th"):
+        assert rel_l2(sim.get(f), ref.get(f)) < tol, (f, rel_l2(sim.get(f), ref.get(f)))
+    e_ref = np.concatenate([ref.get(f).ravel() for f in ("E_r", "E_th", "E_ph")])
+    e_gpu = np.concatenate([sim.get(f).ravel() for f in ("E_r", "E_th", "E_ph")])
+    assert rel_l2(e_gpu, e_ref) < tol
 
 
 def test_split_monopole_field_step_parity(env):

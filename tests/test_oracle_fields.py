@@ -425,3 +425,51 @@ def test_failure_counters(oracle_mod):
     er[3, 4] = np.nan
     o.set("E_r", er)
     assert o.diagnostics()[0].nonfinite_fields == 1
+
+
+def test_fourth_difference_filter_removes_the_odd_even_mode(oracle_mod):
+    """The optional filter of E_r along r and E_th along theta (sigma = 1):
+    with B = 0 the node renormalisation is idle, so the correction stage
+    applies the filter alone.  A cubic in the index is left exactly as it is,
+    the odd-even pattern (-1)^i (resp. (-1)^j) is removed exactly away from
+    the ends, and each component is filtered only along its own direction."""
+    n = 24
+    cfg = dict(nr=n, nt=n, r_min=1.0, r_max=8.0, r_lc=3.0, geom="uniform", b_star=1.0, capacity=0,
+               psi_break=[-1.0], f_break=[1.0], ff_delta_only=1, ff_filter=1.0, r_abs=7.0)
+    o = oracle_mod.Oracle(cfg)
+    for name in ("B_r", "B_th", "B_ph", "E_ph"):
+        o.set(name, np.zeros(o.shape(name)))
+    i = np.arange(n)[:, None] * np.ones((1, n + 1))
+    jj = np.arange(n + 1)[None, :] * np.ones((n, 1))
+    cubic = 0.3 + 0.01 * i - 2e-4 * i ** 2 + 3e-6 * i ** 3 + 0.05 * np.sin(jj)   # any shape along theta
+    o.set("E_r", cubic + 0.7 * (-1.0) ** i)
+    it = np.arange(n + 1)[:, None] * np.ones((1, n))
+    j = np.arange(n)[None, :] * np.ones((n + 1, 1))
+    cubic_t = -0.2 + 0.02 * j - 1e-4 * j ** 3 + 0.03 * np.cos(it)                # any shape along r
+    et0 = cubic_t + 0.4 * (-1.0) ** j
+    et0[0, :] = et0[-1, :] = 0.0
+    o.set("E_th", et0)
+    o.step(1, oracle_mod.ST["correct"])
+    er, et = o.get("E_r"), o.get("E_th")
+    assert np.abs(er[2:n - 2] - cubic[2:n - 2]).max() < 1e-12
+    assert np.array_equal(er[:2], (cubic + 0.7 * (-1.0) ** i)[:2])          # no five-point stencil there
+    assert np.abs(et[1:n, 2:n - 2] - cubic_t[1:n, 2:n - 2]).max() < 1e-12
+    assert np.array_equal(et[1:n, :2], et0[1:n, :2])
+
+
+def test_periodic_literal_return_switches_the_reading(oracle_mod):
+    """ff_return_every = 1 is the literal return on every step, bit for bit;
+    with a period of 2 the first step (index 0) is literal and the second
+    the corrections alone, so after two steps the run differs from both."""
+    from paper_2406_14512_gb300 import workloads
+    base = workloads.config("small_michel")
+    base.update(capacity=0, inject=False, psi_break=[-1.0], f_break=[1.0])
+    runs = {}
+    for tag, kw in {"lit": dict(ff_delta_only=0), "every1": dict(ff_delta_only=1, ff_return_every=1),
+                    "delta": dict(ff_delta_only=1), "every2": dict(ff_delta_only=1, ff_return_every=2)}.items():
+        o = oracle_mod.Oracle(dict(base, **kw))
+        o.step(2)
+        runs[tag] = np.concatenate([o.get(n).ravel() for n in ("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph")])
+    assert np.array_equal(runs["every1"], runs["lit"])
+    assert not np.array_equal(runs["every2"], runs["lit"])
+    assert not np.array_equal(runs["every2"], runs["delta"])
