@@ -162,11 +162,6 @@ typedef struct hff_config {
                                node corrections cannot act on it; sigma = 1
                                removes it, and a smooth field changes by O(h^4)
                                per step.  0 = off (a reading: the paper is silent) */
-  int32_t ff_return_every;  /* with ff_delta_only = 1: on the steps whose index
-                               (the step counter before the step) is a multiple
-                               of this value (> 0) the corrected field itself
-                               returns, as with ff_delta_only = 0; the
-                               corrections alone on the others (0 = never)       */
 } hff_config;
 
 typedef struct hff_info {

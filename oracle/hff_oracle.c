@@ -453,9 +453,8 @@ static void node_pass_b(ost *s) {
       for (int k = 0; k < 3; ++k) NODE(13 + k, i, j) = sc * ep[k] - e[k];
     }
   /* reading "interpolate these back" literally: the corrected node field
-   * E'' = E + Delta E itself returns to the edges (every step, or on the
-   * steps of ff_return_every)                                              */
-  if (!s->c.ff_delta_only || (s->c.ff_return_every > 0 && s->step % s->c.ff_return_every == 0))
+   * E'' = E + Delta E itself returns to the edges                         */
+  if (!s->c.ff_delta_only)
     for (int i = 1; i < nr; ++i)
       for (int j = 0; j <= nt; ++j) {
         double e[3], b[3];
@@ -497,9 +496,6 @@ static double d4_et(const ost *s, int i, int j) {
 
 static void correct_e(ost *s) {
   int nr = s->nr, nt = s->nt, lit = s->c.ff_delta_only == 0;
-  /* reading: the corrected field itself may return once every
-   * ff_return_every steps, the corrections alone in between               */
-  if (!lit && s->c.ff_return_every > 0 && s->step % s->c.ff_return_every == 0) lit = 1;
   double sg = s->c.ff_filter / 16.0;
   double *fr = NULL, *ft = NULL;
   if (sg != 0.0) { /* the filter terms from the uncorrected E */

@@ -84,9 +84,6 @@ typedef struct or_config {
   double ff_filter;          /* sigma of the fourth-difference filter of E_r
                                 along r and E_th along theta where f > 0
                                 (0 = off; 1 removes the odd-even mode)      */
-  int32_t ff_return_every;   /* with ff_delta_only = 1: on steps whose index
-                                is a multiple of this (> 0) the corrected
-                                field itself returns (0 = never)            */
 } or_config;
 
 typedef struct or_diag {

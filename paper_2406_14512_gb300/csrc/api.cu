@@ -122,7 +122,6 @@ int validate(const hff_config *c) {
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
   if (!(c->ff_filter >= 0.0 && c->ff_filter <= 1.0)) return fail(HFF_ERR_ARG, "ff_filter must be in [0, 1]");
-  if (c->ff_return_every < 0) return fail(HFF_ERR_ARG, "ff_return_every must be >= 0");
   if (c->inject_species[0] != c->inject_species[1])
     for (int k = 0; k < 2; ++k)
       if (c->inject_species[k] < 0 || c->inject_species[k] >= c->n_species)
@@ -385,7 +384,6 @@ void fill_params(hff_handle *h) {
     p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
     p.ff_interp_e = c.ff_delta_only ? 0 : 1;
     p.ff_sigma16 = (R)(c.ff_filter / 16.0);
-    p.ff_return_every = c.ff_delta_only ? c.ff_return_every : 0;
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
     p.pushed = h->small->pushed;
@@ -1522,8 +1520,7 @@ static bool same_run(const hff_config &a, const hff_config &b) {
             a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
             a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s &&
             a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1] &&
-            (a.ff_delta_only != 0) == (b.ff_delta_only != 0) && a.ff_filter == b.ff_filter &&
-            a.ff_return_every == b.ff_return_every;
+            (a.ff_delta_only != 0) == (b.ff_delta_only != 0) && a.ff_filter == b.ff_filter;
   for (int k = 0; k < 4; ++k)
     eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
   return eq;

@@ -297,14 +297,6 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
   }
 }
 
-// The corrected field itself returns on this step: always with ff_interp_e,
-// else on the steps (device counter before the step) that ff_return_every
-// divides.
-template <typename R>
-__device__ __forceinline__ bool literal_step(const Params<R> &p) {
-  return p.ff_return_every > 0 && (*p.step % p.ff_return_every) == 0;
-}
-
 // ----------------------------------------------------------- node pass B
 // Renormalisation at interior nodes from E^{n+1} and B^{n+1/2}:
 // E' = E - (E.B) B/B^2 (Eq. 25), E'' = sqrt(B^2/E'^2) E' if E'^2 > B^2 (Eq. 26).
@@ -348,7 +340,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
       d2 = sc * z - e[2];
       clamped = e2 > b2;
     }
-    if (p.ff_interp_e || literal_step(p)) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
+    if (p.ff_interp_e) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
   }
   // running count of Eq. 26 activations (failure detection: a force-free
   // region that keeps needing the clamp is going unstable)
@@ -370,7 +362,7 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   const Fields<R> &f = p.f;
-  const bool lit = p.ff_interp_e != 0 || literal_step(p);
+  const bool lit = p.ff_interp_e != 0;
   const bool filt = p.ff_sigma16 != R(0);
   if (i < nr) {
     const int64_t k = ix(i, j, n1);

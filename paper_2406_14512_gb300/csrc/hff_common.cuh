@@ -164,7 +164,6 @@ struct Params {
   int n_inj, inj_sp[2];     // species created together by the injection
   int ff_interp_e;          // 1: the corrected node E returns to the edges, 0: only Delta E
   R ff_sigma16;             // fourth-difference filter of E_r (r) and E_th (theta): sigma / 16
-  int ff_return_every;      // with ff_interp_e = 0: the corrected field returns on these steps
   R w_inj;
   double *acc;              // [4] injected, killed, radiated, nonfinite
   unsigned long long *pushed;  // [2] live particles pushed: tiled kernel, tail kernel

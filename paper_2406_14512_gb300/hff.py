@@ -58,7 +58,7 @@ class hff_config(C.Structure):
         ("capacity", C.c_int64), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
         ("sort_every", C.c_int32), ("precision", C.c_int32),
         ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
-        ("ff_delta_only", C.c_int32), ("ff_filter", C.c_double), ("ff_return_every", C.c_int32),
+        ("ff_delta_only", C.c_int32), ("ff_filter", C.c_double),
     ]
 
 
@@ -183,7 +183,6 @@ def config_struct(cfg: dict) -> hff_config:
     c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
     c.ff_delta_only = int(cfg.get("ff_delta_only", 0))
     c.ff_filter = float(cfg.get("ff_filter", 0.0))
-    c.ff_return_every = int(cfg.get("ff_return_every", 0))
     return c
 
 

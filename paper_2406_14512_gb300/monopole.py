@@ -86,7 +86,7 @@ def run(n: int = 1024, periods: float = 2.0, chunk: int = 2000, log=None, layer:
     d, prof = sim.diagnostics()
     lm = michel(cfg)["L_M"]
     out = {"n": n, "periods": periods, "layer": layer, "ff_delta_only": cfg.get("ff_delta_only", 0),
-           "ff_filter": cfg.get("ff_filter", 0.0), "ff_return_every": cfg.get("ff_return_every", 0),
+           "ff_filter": cfg.get("ff_filter", 0.0),
            "ppc": cfg["ppc"],
            "steps": steps, "dt": dt, "wall_s": wall,
            "eps": d.eps, "L_in_over_L_M": d.l_in / lm, "L_out_over_L_M": d.l_out / lm,
@@ -108,11 +108,8 @@ def main():
     ap.add_argument("--ppc", type=float, default=4.0, help="largest injected pairs per surface cell")
     ap.add_argument("--ff-filter", type=float, default=0.0,
                     help="sigma of the fourth-difference filter of E_r, E_th (0 = off)")
-    ap.add_argument("--ff-return-every", type=int, default=0,
-                    help="with --ff-delta-only 1: the corrected field itself returns every N steps")
     a = ap.parse_args()
-    kw = {"ff_delta_only": a.ff_delta_only, "ppc": a.ppc, "ff_filter": a.ff_filter,
-          "ff_return_every": a.ff_return_every}
+    kw = {"ff_delta_only": a.ff_delta_only, "ppc": a.ppc, "ff_filter": a.ff_filter}
     print(json.dumps(run(a.n, a.periods, a.chunk, log=lambda m: print(m, file=sys.stderr, flush=True),
                          layer=a.layer, **kw)))
 

@@ -59,23 +59,6 @@ def test_field_step_parity(env, name, prec, tol, extra):
         assert rel_l2(sim.get(f), ref.get(f)) < 10 * tol, f
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-def test_periodic_literal_return_parity(env, prec, tol):
-    """The corrections-only return with the corrected field itself returning
-    every third step (device step counter against the oracle's): five field
-    steps from the same fields, literal on steps 0 and 3."""
-    cfg, sim, ref = make(env, "small_michel", capacity=0, precision=prec, sort_every=0, ff_delta_only=1,
-                         ff_return_every=3)
-    shared_initial_state(sim, ref, seed=5)
-    sim.step_stages(5, FIELD_STAGES)
-    ref.step(5, FIELD_STAGES)
-    for f in ("B_r", "B_th", "B_ph", "E_th"):
-        assert rel_l2(sim.get(f), ref.get(f)) < tol, (f, rel_l2(sim.get(f), ref.get(f)))
-    e_ref = np.concatenate([ref.get(f).ravel() for f in ("E_r", "E_th", "E_ph")])
-    e_gpu = np.concatenate([sim.get(f).ravel() for f in ("E_r", "E_th", "E_ph")])
-    assert rel_l2(e_gpu, e_ref) < tol
-
-
 def test_split_monopole_field_step_parity(env):
     """The split monopole (Michel's solution reversed in the south, its
     current sheet on the equator, force-free everywhere): one field step of

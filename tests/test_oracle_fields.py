@@ -456,20 +456,3 @@ def test_fourth_difference_filter_removes_the_odd_even_mode(oracle_mod):
     assert np.abs(et[1:n, 2:n - 2] - cubic_t[1:n, 2:n - 2]).max() < 1e-12
     assert np.array_equal(et[1:n, :2], et0[1:n, :2])
 
-
-def test_periodic_literal_return_switches_the_reading(oracle_mod):
-    """ff_return_every = 1 is the literal return on every step, bit for bit;
-    with a period of 2 the first step (index 0) is literal and the second
-    the corrections alone, so after two steps the run differs from both."""
-    from paper_2406_14512_gb300 import workloads
-    base = workloads.config("small_michel")
-    base.update(capacity=0, inject=False, psi_break=[-1.0], f_break=[1.0])
-    runs = {}
-    for tag, kw in {"lit": dict(ff_delta_only=0), "every1": dict(ff_delta_only=1, ff_return_every=1),
-                    "delta": dict(ff_delta_only=1), "every2": dict(ff_delta_only=1, ff_return_every=2)}.items():
-        o = oracle_mod.Oracle(dict(base, **kw))
-        o.step(2)
-        runs[tag] = np.concatenate([o.get(n).ravel() for n in ("E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph")])
-    assert np.array_equal(runs["every1"], runs["lit"])
-    assert not np.array_equal(runs["every2"], runs["lit"])
-    assert not np.array_equal(runs["every2"], runs["delta"])
