@@ -46,11 +46,20 @@ def c4():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    free_dev, _ = torch.cuda.mem_get_info()
+    import os
+    free_dev, total_dev = torch.cuda.mem_get_info()
+    short = None
     if free_dev < 170e9:
-        pytest.skip(f"needs 170 GB of free device memory, {free_dev / 1e9:.0f} GB free")
-    if host_available() < 120e9:
-        pytest.skip(f"needs 120 GB of available host memory, {host_available() / 1e9:.0f} GB available")
+        short = f"needs 170 GB of free device memory, {free_dev / 1e9:.0f} GB free"
+    elif host_available() < 120e9:
+        short = f"needs 120 GB of available host memory, {host_available() / 1e9:.0f} GB available"
+    if short:
+        # on a GPU whose memory could hold the workload, missing room is a
+        # failure (the precision-stress workload must not drop out of a run
+        # unnoticed); smaller GPUs, or an explicit opt-out, skip
+        if total_dev >= 200e9 and os.environ.get("HFF_ALLOW_C4_SKIP") != "1":
+            pytest.fail(short + " (set HFF_ALLOW_C4_SKIP=1 to skip)")
+        pytest.skip(short)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2406_14512_gb300 import hff, workloads
