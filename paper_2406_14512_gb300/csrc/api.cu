@@ -29,7 +29,15 @@ int fail(int code, const std::string &m) {
     if (e_ != cudaSuccess) return fail(HFF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-constexpr int kChunk = 8192;  // particles per work item of the tiled push
+// Particles per work item of the tiled push: the largest power of two from
+// 512 to 8192 at or below capacity / 4096, so that a small instance still
+// offers a few thousand items (blocks) to the GPU, while a large one keeps
+// long items that amortise the staging of their tile.
+int chunk_of(const hff_config &c) {
+  int k = 512;
+  while (k < 8192 && (int64_t)(2 * k) * 4096 <= c.capacity) k *= 2;
+  return k;
+}
 
 // ------------------------------------------------------------------ geometry
 // FP64 grid of Sect. 4: r log-spaced, theta uniform, geometric half nodes,
@@ -218,7 +226,8 @@ void layout(const hff_config &c, Offsets &o) {
   o.ntiles = (int)((nr + tr - 1) / tr) * o.ntt;
   o.nb = (int)((cap + 2047) / 2048);
   o.nparts = (int)(((size_t)o.nb * 256 + 4095) / 4096);
-  o.max_items = c.n_species * (o.ntiles + (int)((cap + kChunk - 1) / kChunk)) + 1;
+  const int chunk = chunk_of(c);
+  o.max_items = c.n_species * (o.ntiles + (int)((cap + chunk - 1) / chunk)) + 1;
   if (c.sort_every > 0) {
     for (int s = 0; s < c.n_species; ++s) o.sidx[s] = L.take(cap * 4);
     o.keys_a = L.take(cap * 4); o.keys_b = L.take(cap * 4);
@@ -1053,7 +1062,7 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
   h->wl.n_items = &h->small->n_items;
   h->wl.next = &h->small->next;
   h->wl.max_items = h->o.max_items;
-  h->wl.chunk = kChunk;
+  h->wl.chunk = chunk_of(*cfg);
   h->ss.keys_a = reinterpret_cast<uint32_t *>(h->base + h->o.keys_a);
   h->ss.keys_b = reinterpret_cast<uint32_t *>(h->base + h->o.keys_b);
   h->ss.idx_a = reinterpret_cast<uint32_t *>(h->base + h->o.idx_a);
