@@ -63,11 +63,13 @@ def _cache_write(d: dict) -> None:
     os.replace(tmp, CACHE)
 
 
-def resolve(cfg: dict, particles=None, tiles=None, cadences=None, steps: int = 24, warmup: int = 3,
+def resolve(cfg: dict, particles=None, tiles=None, cadences=None, steps: int = 48, warmup: int = 3,
             use_cache: bool = True) -> dict:
     """The configuration with its launch shape filled in (see the module
     docstring).  A configuration that does not ask for tuning is returned
-    unchanged.  The result carries the probe table under "autotune"."""
+    unchanged.  The result carries the probe table under "autotune".  The
+    timed window (48 steps) is a multiple of every default cadence, so that
+    each candidate is charged its exact share of sorts."""
     if not wants_tuning(cfg):
         return cfg
     n = 0 if particles is None else sum(len(p["cell"]) for p in particles)

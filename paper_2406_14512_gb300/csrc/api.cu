@@ -29,13 +29,20 @@ int fail(int code, const std::string &m) {
     if (e_ != cudaSuccess) return fail(HFF_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Particles per work item of the tiled push: the largest power of two from
-// 512 to 8192 at or below capacity / 4096, so that a small instance still
-// offers a few thousand items (blocks) to the GPU, while a large one keeps
-// long items that amortise the staging of their tile.
+// Particles per work item of the tiled push.  A grid whose tiles already
+// give the GPU enough items (tiles x species >= 4096) keeps 8192, so that
+// every item amortises the staging of its tile; a small instance takes the
+// largest power of two from 512 to 8192 at or below capacity / 4096, so that
+// it still offers a few thousand items (blocks) to the GPU.  Members of an
+// ensemble keep 8192 (the members fill the GPU together, and short items
+// only re-stage their tiles).  The work list is sized for the shortest.
+constexpr int kChunkMin = 512, kChunkMax = 8192;
 int chunk_of(const hff_config &c) {
-  int k = 512;
-  while (k < 8192 && (int64_t)(2 * k) * 4096 <= c.capacity) k *= 2;
+  const int tr = c.tile_r > 0 ? c.tile_r : 16, tt = c.tile_t > 0 ? c.tile_t : 32;
+  const int64_t tiles = (int64_t)((c.nr + tr - 1) / tr) * ((c.nt + tt - 1) / tt);
+  if (tiles * c.n_species >= 4096) return kChunkMax;
+  int k = kChunkMin;
+  while (k < kChunkMax && (int64_t)(2 * k) * 4096 <= c.capacity) k *= 2;
   return k;
 }
 
@@ -226,8 +233,7 @@ void layout(const hff_config &c, Offsets &o) {
   o.ntiles = (int)((nr + tr - 1) / tr) * o.ntt;
   o.nb = (int)((cap + 2047) / 2048);
   o.nparts = (int)(((size_t)o.nb * 256 + 4095) / 4096);
-  const int chunk = chunk_of(c);
-  o.max_items = c.n_species * (o.ntiles + (int)((cap + chunk - 1) / chunk)) + 1;
+  o.max_items = c.n_species * (o.ntiles + (int)((cap + kChunkMin - 1) / kChunkMin)) + 1;
   if (c.sort_every > 0) {
     for (int s = 0; s < c.n_species; ++s) o.sidx[s] = L.take(cap * 4);
     o.keys_a = L.take(cap * 4); o.keys_b = L.take(cap * 4);
@@ -984,6 +990,7 @@ int hff_init(const hff_config *cfg, int n_inst, void *dev_mem, size_t bytes, voi
     const size_t b = planned_bytes(cfg[k]);
     rc = init_one(&cfg[k], (char *)dev_mem + off, b, stream, &m);
     if (rc != HFF_OK) return bail(fail(rc, "instance " + std::to_string(k) + ": " + g_err));
+    m->wl.chunk = kChunkMax;  // see chunk_of
     e->members.push_back(m);
     off += b;
     cudaStream_t f = nullptr;
