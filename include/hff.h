@@ -97,6 +97,10 @@ extern "C" {
 #define HFF_ST_INJECT 64   /* surface pair injection                            */
 #define HFF_ST_SORT 128    /* stable tile sort + compaction (on its cadence)     */
 #define HFF_ST_ALL 255
+#define HFF_ST_NOCOUNT 256 /* with stages that exclude INJECT: run them without
+                              advancing the step counter (one step split into
+                              stage groups with exchanges in between counts
+                              once, at its INJECT group)                        */
 /* order of execution: NODE, PUSH, FARADAY1, AMPERE, CORRECT, FARADAY2,
  * INJECT, SORT */
 
@@ -110,7 +114,10 @@ typedef struct hff_config {
   double b_star;            /* surface field scale: mu = b_star r_min^3          */
   int32_t geom;             /* HFF_GEOM_*                                         */
   double courant;           /* fraction of the 2D CFL limit, (0, 0.9]            */
-  double r_abs;             /* start of the absorbing layer (Sect. 4: 3 R_LC)    */
+  double r_abs;             /* start of the absorbing layer (Sect. 4: 3 R_LC);
+                               >= 3 cells inside r_max, or >= r_max for a grid
+                               without an absorbing layer (a slab of a larger
+                               run)                                              */
   double absorb_strength;   /* damping per step at r_max (cubic ramp from r_abs) */
   int32_t n_breaks;         /* 0..4 breakpoints of f; 0 means f = 0 (pure PIC)   */
   double psi_break[4];      /* in units of Psi_pc = mu/R_LC (dipolar fields) or
@@ -240,7 +247,10 @@ int hff_load_particles(hff_handle *h, int inst, int species, int64_t n, const in
                        const void *xo, const void *yo, const void *ur, const void *ut,
                        const void *up, const void *w, int where);
 
-/* Overwrite field `which` (0..5) with `bytes` bytes from src (host or device).
+/* Overwrite field `which` (0..5, or 6..8 for J_PIC) with `bytes` bytes from
+ * src (host or device).  Setting J between the push and Ampere's law of a
+ * step split into stage groups adds current deposited elsewhere (for
+ * instance the neighbour's share in a decomposed run).
  * B is held as the initial field B_0 plus a perturbation (the Yee update
  * advances the perturbation, with curl B_0 precomputed in FP64), so setting
  * B stores B - B_0 and reading it (hff_fields) returns the sum, each rounded

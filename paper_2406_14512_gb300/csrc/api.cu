@@ -130,7 +130,8 @@ int validate(const hff_config *c) {
   if (c->precision != HFF_FP32 && c->precision != HFF_FP64) return fail(HFF_ERR_ARG, "bad precision");
   const double dlog = std::log(c->r_max / c->r_min) / c->nr;
   const double xi_abs = std::log(c->r_abs / c->r_min) / dlog;
-  if (!(c->r_abs > c->r_min) || xi_abs > c->nr - 3) return fail(HFF_ERR_ARG, "r_abs must lie >= 3 cells inside r_max");
+  if (!(c->r_abs > c->r_min) || (xi_abs > c->nr - 3 && c->r_abs < c->r_max))
+    return fail(HFF_ERR_ARG, "r_abs must lie >= 3 cells inside r_max, or at or beyond r_max (no absorber)");
   if (c->tile_r < 0 || c->tile_t < 0 || c->tile_r > 64 || c->tile_t > 128)
     return fail(HFF_ERR_ARG, "tile out of range");
   if (!(c->gamma_th == 0 || c->gamma_th > 1) || (c->gamma_th > 0 && !(c->gamma_s >= 1.0)))
@@ -621,7 +622,7 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
   if (stages & HFF_ST_CORRECT) launch_correct<R>(p, s);
   if (stages & HFF_ST_FARADAY2) launch_faraday<R>(p, R(0.5), true, s);
   if (stages & HFF_ST_INJECT) launch_inject<R>(p, s);
-  else launch_step_done<R>(p, s);
+  else if (!(stages & HFF_ST_NOCOUNT)) launch_step_done<R>(p, s);
   CK(cudaGetLastError());
   return HFF_OK;
 }
@@ -811,6 +812,7 @@ int do_stages(hff_handle *h, int32_t n, int32_t stages) {
   for (int32_t k = 0; k < n; ++k) {
     rc = enqueue_step<R>(h, h->parity, stages, h->st);
     if (rc != HFF_OK) return rc;
+    if ((stages & HFF_ST_NOCOUNT) && !(stages & HFF_ST_INJECT)) continue;
     h->step++;
     if ((stages & HFF_ST_SORT) && h->c.sort_every > 0 && h->step % h->c.sort_every == 0) {
       rc = run_sort_now<R>(h, h->st);
@@ -1194,11 +1196,12 @@ static size_t field_elem_bytes(const hff_handle *h, int which) {
 
 int hff_set_field(hff_handle *h, int inst, int which, const void *src, size_t bytes, int where) {
   h = member(h, inst);
-  if (!h || which < 0 || which > 5 || !src) return fail(HFF_ERR_ARG, "bad arguments");
+  if (!h || which < 0 || which > 8 || !src) return fail(HFF_ERR_ARG, "bad arguments");
   const size_t R = h->c.precision == HFF_FP64 ? 8 : 4;
   if (bytes != (size_t)field_elems(h, which) * R) return fail(HFF_ERR_ARG, "byte count does not match the field");
-  if (which < 3) {
-    CK(cudaMemcpyAsync(h->base + h->o.f[which], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  if (which < 3 || which >= 6) {  // E, or J_PIC (offset table slots 9..11)
+    const int slot = which < 3 ? which : which + 3;
+    CK(cudaMemcpyAsync(h->base + h->o.f[slot], src, bytes, where == HFF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
   } else {  // B is held as B_0 + dB: store dB = B - B_0
     const void *b = src;
     if (where == HFF_HOST) {  // stage through the FP64 node scratch (>= any field)

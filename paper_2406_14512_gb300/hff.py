@@ -31,7 +31,7 @@ HFF_OK, HFF_ERR_ARG, HFF_ERR_CAPACITY, HFF_ERR_CUDA, HFF_ERR_TIMEOUT, HFF_ERR_NO
 GEOM = {"dipole": 0, "monopole": 1, "synth": 2, "uniform": 3, "michel": 4}
 FP32, FP64 = 0, 1
 HOST, DEVICE = 0, 1
-ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255)
+ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255, nocount=256)
 SCALAR_RR_SCALE = 0
 FIELDS = ["E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph", "J_r", "J_th", "J_ph", "psi",
           "jperp_r", "jperp_th", "jperp_ph", "dE_r", "dE_th", "dE_ph",

@@ -29,6 +29,7 @@ runs with the gloo backend on CPU ranks.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -256,3 +257,76 @@ class SlabRun:
             self.e.stages(ST_INJECT)
             self.e.count_step()
             self.migrate()
+
+
+def slab_config(cfg: dict, lo: int, hi: int) -> dict:
+    """The configuration of a slab on node rows lo .. hi of the run `cfg`:
+    the same log grid cut at r_lo and r_hi, the same magnetic moment (flux
+    unit) and time step, injection only on the slab that holds the star.  An
+    absorber start beyond the slab's r_max leaves the slab without one."""
+    d = math.log(cfg["r_max"] / cfg["r_min"]) / cfg["nr"]
+    r_lo, r_hi = cfg["r_min"] * math.exp(lo * d), cfg["r_min"] * math.exp(hi * d)
+    c = dict(cfg, nr=hi - lo, r_min=r_lo, r_max=r_hi, inject=bool(cfg.get("inject")) and lo == 0)
+    mono = cfg.get("geom") in ("monopole", "michel")
+    c["b_star"] = cfg.get("b_star", 1.0) * (cfg["r_min"] / r_lo) ** (2 if mono else 3)
+    c["r_abs"] = cfg.get("r_abs", 3.0 * cfg["r_lc"])
+    c["shell_r"] = cfg.get("shell_r", 2.0 * cfg["r_min"])
+    c["courant"] = cfg.get("courant", 0.5) * _min_cell_limit(cfg) / _min_cell_limit(c)
+    return c
+
+
+def _min_cell_limit(c: dict) -> float:
+    """The 2D light-crossing limit of the smallest cell of a log grid, which
+    the Courant rule scales (the innermost cell)."""
+    d, dth = math.log(c["r_max"] / c["r_min"]) / c["nr"], math.pi / c["nt"]
+    dr = c["r_min"] * (math.exp(d) - 1.0)
+    return 1.0 / math.sqrt(1.0 / dr ** 2 + 1.0 / (c["r_min"] * dth) ** 2)
+
+
+class LibrarySlab:
+    """A slab computed by the CUDA library: one instance (hff.Sim) on the
+    slab's local rows, stepped in stage groups with hff_step_stages (the
+    first two groups do not count a step; the injection group does).
+
+    fields: global E and B arrays (node- and half-row shaped, as hff_fields
+    returns them) that initialise the slab's rows."""
+
+    HALF = {"E_r", "B_th", "B_ph", "J_r"}
+
+    def __init__(self, cfg: dict, lo: int, hi: int, fields: dict, device: str = "cuda:0"):
+        from . import hff
+        self.hff = hff
+        self.cfg = slab_config(cfg, lo, hi)
+        self.sim = hff.Sim(self.cfg, device=device)
+        self.lo, self.hi, self.nt, self.n_species = lo, hi, cfg["nt"], len(cfg.get("q", [-1.0, 1.0]))
+        for name, a in fields.items():
+            self.sim.set(name, a[lo:hi if name in self.HALF else hi + 1])
+
+    def stages(self, mask: int) -> None:
+        st = self.hff.ST
+        if not mask & st["inject"]:
+            mask |= st["nocount"]
+        self.sim.step_stages(1, mask)
+
+    def count_step(self) -> None:
+        pass  # the injection group counted it
+
+    def get(self, name: str):
+        return self.sim.get(name).astype(np.float64)
+
+    def set(self, name: str, a) -> None:
+        self.sim.set(name, a)
+
+    def particles(self, s: int) -> dict:
+        p = self.sim.particles(s)
+        c = p["cell"]
+        p["cell"] = np.where(c >= 0, c + self.lo * self.nt, -1).astype(np.int32)
+        return p
+
+    def set_particles(self, s: int, p: dict) -> None:
+        q = {k: np.asarray(v) for k, v in p.items()}
+        q["cell"] = np.where(q["cell"] >= 0, q["cell"] - self.lo * self.nt, -1).astype(np.int32)
+        self.sim.load(s, q)
+
+    def close(self) -> None:
+        self.sim.close()

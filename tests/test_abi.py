@@ -47,7 +47,7 @@ def test_plan_sizes_scale_with_grid_and_capacity(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=33), dict(n_breaks_bad=True),
-                                 dict(r_abs=1e9), dict(precision_bad=True)])
+                                 dict(r_abs="one_cell_inside"), dict(precision_bad=True)])
 def test_invalid_configs_are_rejected(lib, bad):
     cfg = workloads.config("small_pic")
     cfg.update(capacity=10)
@@ -61,8 +61,8 @@ def test_invalid_configs_are_rejected(lib, bad):
     if "n_breaks_bad" in bad:
         c.n_breaks = 2
         c.psi_break[0], c.psi_break[1] = 2.0, 1.0
-    if "r_abs" in bad:
-        c.r_abs = bad["r_abs"]
+    if "r_abs" in bad:  # inside r_max but closer than 3 cells to it (r_abs >= r_max means no absorber)
+        c.r_abs = c.r_max * (c.r_max / c.r_min) ** (-1.0 / c.nr)
     if "precision_bad" in bad:
         c.precision = 7
     with pytest.raises(hff.HffError) as e:
