@@ -170,6 +170,8 @@ struct Offsets {
   size_t sidx[kMaxSpecies];  // sorted order of the last sort, per species
   size_t items;
   size_t qnode, rows, psi64;
+  size_t fsnap;          // halo snapshot of the fused field update
+  int seg_rows;          // rows per segment of the fused field update
   size_t ev[8];          // pair-creation events: key cell xo yo ur ut up w
   size_t spec;           // spectrum bins (on request)
   int64_t ev_cap;
@@ -252,6 +254,10 @@ void layout(const hff_config &c, Offsets &o) {
   o.qnode = L.take(nn * 8);
   o.rows = L.take((nr + 1) * 8 * 8);
   o.psi64 = L.take(nn * 8);
+  // the fused field update's segments are sized for the 152 SMs of a GB300
+  // (a property of the grid, not of the device, so that hff_plan needs no GPU)
+  o.seg_rows = fuse_seg_rows(c.nr, c.nt, 152);
+  o.fsnap = L.take(fuse_snap_bytes(c.nr, c.nt, o.seg_rows, R));
   o.total = (L.off + 255) & ~size_t(255);
 }
 
@@ -617,10 +623,20 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
     return HFF_OK;
   }
   if (stages & HFF_ST_PUSH) launch_push_tail<R>(p, s, h->tail_grid);
-  if (stages & HFF_ST_FARADAY1) launch_faraday<R>(p, R(0.5), false, s);
-  if (stages & HFF_ST_AMPERE) launch_ampere<R>(p, s);
-  if (stages & HFF_ST_CORRECT) launch_correct<R>(p, s);
-  if (stages & HFF_ST_FARADAY2) launch_faraday<R>(p, R(0.5), true, s);
+  constexpr int kFieldStages = HFF_ST_FARADAY1 | HFF_ST_AMPERE | HFF_ST_CORRECT | HFF_ST_FARADAY2;
+  if ((stages & kFieldStages) == kFieldStages) {
+    // the whole field update in one pass; J_PIC cleared for the next deposit
+    launch_field_fused<R>(p, h->o.seg_rows, h->base + h->o.fsnap, s);
+    const int64_t nr = h->c.nr, nt = h->c.nt;
+    CK(cudaMemsetAsync(p.f.jr, 0, (size_t)(nr * (nt + 1)) * sizeof(R), s));
+    CK(cudaMemsetAsync(p.f.jt, 0, (size_t)((nr + 1) * nt) * sizeof(R), s));
+    CK(cudaMemsetAsync(p.f.jp, 0, (size_t)((nr + 1) * (nt + 1)) * sizeof(R), s));
+  } else {
+    if (stages & HFF_ST_FARADAY1) launch_faraday<R>(p, R(0.5), false, s);
+    if (stages & HFF_ST_AMPERE) launch_ampere<R>(p, s);
+    if (stages & HFF_ST_CORRECT) launch_correct<R>(p, s);
+    if (stages & HFF_ST_FARADAY2) launch_faraday<R>(p, R(0.5), true, s);
+  }
   if (stages & HFF_ST_INJECT) launch_inject<R>(p, s);
   else if (!(stages & HFF_ST_NOCOUNT)) launch_step_done<R>(p, s);
   CK(cudaGetLastError());
@@ -1091,6 +1107,9 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
     const size_t psm = cfg->precision == HFF_FP64 ? psi_smem<double>(cfg->nt) : psi_smem<float>(cfg->nt);
     const cudaError_t e = cfg->precision == HFF_FP64 ? set_psi_smem<double>(psm) : set_psi_smem<float>(psm);
     if (e != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the flux-prefix shared memory size"));
+    const cudaError_t e2 = cfg->precision == HFF_FP64 ? set_field_fused_smem<double>(field_fused_smem<double>())
+                                                      : set_field_fused_smem<float>(field_fused_smem<float>());
+    if (e2 != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the fused field update's shared memory size"));
   }
   if (cfg->precision == HFF_FP32) {
     fill_params<float>(h);

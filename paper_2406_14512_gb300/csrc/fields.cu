@@ -13,6 +13,8 @@
 // once in FP64.  In FP32 the rounding of B then scales with |dB| instead of
 // |B|: near the star of a fine grid the rounding of a stored |B| ~ 1, divided
 // by a cell of 1e-3 r*, would otherwise enter E every step through the curl.
+#include <algorithm>
+
 #include "hff_common.cuh"
 
 namespace hff {
@@ -396,6 +398,428 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   }
 }
 
+// ------------------------------------------------------- fused field update
+// The field update between the push and the injection -- Faraday's first
+// half step (Eq. 18), Ampere's law with the blended current (Eqs. 19, 28) and
+// the boundaries, the renormalisation at the nodes (Eqs. 25-26), the return to
+// the edges with the blend weights, and Faraday's second half step with the
+// absorber -- as one pass.  A block owns a strip of theta columns (with a
+// halo of kFuseHalo columns on each side, recomputed) and a segment of rows
+// (with kFuseWarm rows of warm-up below it, recomputed), and walks the rows
+// upward.  At row step k it loads node row k and half row k (k+1/2) of E^n,
+// dB^n, B_0, J_perp and Psi into ring buffers in shared memory, and then:
+//   F1: B^{n+1/2} at node row k (B_r) and half row k-1 (B_th, B_ph);
+//   A : E^{n+1} at half row k-1 (E_r) and node row k-1 (E_th, E_ph), J cleared;
+//   N : Delta E (or E'') at node row k-1, and the filter terms;
+//   C : the corrected E at half row k-3 and node row k-3;
+//   F2: dB^{n+1} at node row k-3 (B_r) and half row k-4 (B_th, B_ph).
+// Each stage reads only rows the earlier stages of this or previous steps
+// produced, so every value is computed once per block from E^n and dB^n read
+// once; the outputs are written once.  The arithmetic is that of k_faraday,
+// k_ampere, k_node_b and k_correct, location by location.
+//
+// The update is in place, and a block's halo columns and warm-up / trailing
+// rows belong to its neighbours, which overwrite them during the same
+// launch; so a block reads E^n and dB^n live only inside its own area (which
+// no other block writes, and which it overwrites only rows below the one it
+// is reading), and everywhere else from a snapshot of those regions taken
+// just before (k_fuse_snap).  J_PIC, read inside the halos too, is cleared by
+// the caller after the launch.
+constexpr int kFuseThreads = 128;     // columns of a strip, halo included
+constexpr int kFuseHalo = 8;          // columns recomputed on each side
+constexpr int kFuseWarm = 8;          // rows recomputed below a segment
+// ring depths (rows live at once, see the step order above)
+constexpr int kDEn = 2, kDBh = 4, kDB0n = 2, kDB0h = 3, kDJp = 2, kDPsi = 4, kDEnr = 5, kDEnn = 3, kDD = 3,
+              kDEc = 2;
+
+template <typename R>
+struct FuseRings {
+  R *en_r, *en_t, *en_p;        // E^n            (half, node, node)   kDEn
+  R *dbn_t, *dbn_p;             // dB^n           (half, half)         kDEn
+  R *b0_r, *b0_t, *b0_p;        // B_0            (node, half, half)   kDB0n, kDB0h
+  R *jp_r, *jp_t, *jp_p;        // J_perp         (node)               kDJp
+  typename PsiOf<R>::T *psi;    // Psi            (node)               kDPsi
+  R *bh_r, *bh_t, *bh_p;        // dB^{n+1/2}     (node, half, half)   kDBh
+  R *e1_r, *e1_t, *e1_p;        // E^{n+1} before the correction (half kDEnr, node kDEnn)
+  R *d_r, *d_t, *d_p;           // Delta E or E'' (node)               kDD
+  R *ec_r, *ec_t, *ec_p;        // corrected E    (half, node, node)   kDEc
+};
+
+template <typename R>
+size_t fuse_smem_bytes() {
+  const size_t rows = 3 * kDEn + 2 * kDEn + kDB0n + 2 * kDB0h + 3 * kDJp + 3 * kDBh + kDEnr + 2 * kDEnn + 3 * kDD +
+                      3 * kDEc;
+  return rows * kFuseThreads * sizeof(R) + (size_t)kDPsi * kFuseThreads * sizeof(typename PsiOf<R>::T) + 64;
+}
+
+// Geometry of a launch: strips of kFuseOwn owned columns, segments of
+// seg_rows owned rows.  Snapshot of E^n and dB^n (six arrays, every array
+// addressed as (nr+1) x (nt+1)): for every strip boundary b = 1 .. strips-1
+// the 2 kFuseHalo columns around column b kFuseOwn over all rows, and for
+// every segment boundary b = 1 .. segs-1 the rows from b seg_rows - kFuseWarm
+// to b seg_rows + kFuseTrail - 1 over all columns.
+constexpr int kFuseOwn = kFuseThreads - 2 * kFuseHalo;
+constexpr int kFuseTrail = 5;   // rows above a segment the pipeline reads (k1 = i_e + 4)
+constexpr int kFuseArrays = 6;  // E_r E_th E_ph dB_r dB_th dB_ph
+struct FuseGeom {
+  int strips, segs, seg_rows;
+};
+__host__ __device__ inline FuseGeom fuse_geom(int nr, int nt, int seg_rows) {
+  FuseGeom g;
+  g.strips = (nt + 1 + kFuseOwn - 1) / kFuseOwn;
+  g.seg_rows = seg_rows;
+  g.segs = (nr + 1 + seg_rows - 1) / seg_rows;
+  return g;
+}
+__host__ __device__ inline int64_t fuse_snap_cols(int nr, int strips) {
+  return (int64_t)(strips > 1 ? strips - 1 : 0) * kFuseArrays * (nr + 1) * (2 * kFuseHalo);
+}
+__host__ __device__ inline int64_t fuse_snap_rows(int nt, int segs) {
+  return (int64_t)(segs > 1 ? segs - 1 : 0) * kFuseArrays * (kFuseWarm + kFuseTrail) * (nt + 1);
+}
+
+template <typename R>
+__device__ __forceinline__ const R *fuse_array(const Params<R> &p, int a, int &ld, int &rows, int &cols) {
+  const int nr = p.nr, nt = p.nt;
+  switch (a) {
+    case 0: ld = nt + 1; rows = nr; cols = nt + 1; return p.f.er;
+    case 1: ld = nt; rows = nr + 1; cols = nt; return p.f.et;
+    case 2: ld = nt + 1; rows = nr + 1; cols = nt + 1; return p.f.ep;
+    case 3: ld = nt; rows = nr + 1; cols = nt; return p.f.br;
+    case 4: ld = nt + 1; rows = nr; cols = nt + 1; return p.f.bt;
+    default: ld = nt; rows = nr; cols = nt; return p.f.bp;
+  }
+}
+
+// the snapshot (one thread per snapshot element)
+template <typename R>
+__global__ void k_fuse_snap(Params<R> p, R *snap_c, R *snap_r, FuseGeom fg) {
+  const int nr = p.nr, nt = p.nt;
+  const int64_t nc = fuse_snap_cols(nr, fg.strips), nrw = fuse_snap_rows(nt, fg.segs);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc + nrw; e += (int64_t)gridDim.x * blockDim.x) {
+    int b, a, row, col;
+    if (e < nc) {
+      const int w = 2 * kFuseHalo;
+      int64_t q = e;
+      const int cc = (int)(q % w); q /= w;
+      row = (int)(q % (nr + 1)); q /= (nr + 1);
+      a = (int)(q % kFuseArrays); b = (int)(q / kFuseArrays) + 1;
+      col = b * kFuseOwn - kFuseHalo + cc;
+    } else {
+      const int h = kFuseWarm + kFuseTrail;
+      int64_t q = e - nc;
+      col = (int)(q % (nt + 1)); q /= (nt + 1);
+      const int rr = (int)(q % h); q /= h;
+      a = (int)(q % kFuseArrays); b = (int)(q / kFuseArrays) + 1;
+      row = b * fg.seg_rows - kFuseWarm + rr;
+    }
+    int ld, rows, cols;
+    const R *src = fuse_array(p, a, ld, rows, cols);
+    const R v = (row >= 0 && row < rows && col >= 0 && col < cols) ? src[(int64_t)row * ld + col] : R(0);
+    if (e < nc) snap_c[e] = v;
+    else snap_r[e - nc] = v;
+  }
+}
+
+// ring slot of a row (rows may be negative for never-used slots)
+__device__ __forceinline__ int rs(int row, int depth) { return ((row % depth) + depth) % depth; }
+
+template <typename R>
+__global__ void __launch_bounds__(kFuseThreads) k_field_fused(Params<R> p, R hdt, FuseGeom fg, const R *snap_c,
+                                                              const R *snap_r) {
+  using P = typename PsiOf<R>::T;
+  extern __shared__ __align__(16) unsigned char fsmem[];
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1, NC = kFuseThreads, seg_rows = fg.seg_rows;
+  const int c = threadIdx.x, sx = blockIdx.x, sy = blockIdx.y;
+  const int j = sx * kFuseOwn - kFuseHalo + c;                          // global column of this thread
+  const bool jn = j >= 0 && j <= nt, jh = j >= 0 && j < nt;          // node / half column exists
+  const bool own = c >= kFuseHalo && c < NC - kFuseHalo;               // column written by this block
+  const int i_s = sy * seg_rows;                                       // first output row
+  if (i_s > nr) return;
+  const int i_e = min(i_s + seg_rows, nr + 1);                         // one past the last output node row
+  // E^n and dB^n at (row, column j): live inside this block's own area,
+  // from the snapshot in the halo columns and the warm-up / trailing rows
+  auto src = [&](int a, const R *live, int ld, int row) -> R {
+    if (own && row >= i_s && row < i_e) return live[(int64_t)row * ld + j];
+    if (!own) {
+      const int b = (c < kFuseHalo) ? sx : sx + 1;                     // strip boundary
+      const int cc = j - (b * kFuseOwn - kFuseHalo);
+      return snap_c[(((int64_t)(b - 1) * kFuseArrays + a) * (nr + 1) + row) * (2 * kFuseHalo) + cc];
+    }
+    const int b = (row < i_s) ? sy : sy + 1;                           // segment boundary
+    const int rr = row - (b * seg_rows - kFuseWarm);
+    return snap_r[(((int64_t)(b - 1) * kFuseArrays + a) * (kFuseWarm + kFuseTrail) + rr) * (nt + 1) + j];
+  };
+  const int k0 = max(0, i_s - kFuseWarm), k1 = min(nr, i_e) + 4;
+  // carve the rings
+  FuseRings<R> g;
+  {
+    R *q = reinterpret_cast<R *>(fsmem);
+    auto take = [&](int rows) { R *r = q; q += rows * NC; return r; };
+    g.en_r = take(kDEn); g.en_t = take(kDEn); g.en_p = take(kDEn);
+    g.dbn_t = take(kDEn); g.dbn_p = take(kDEn);
+    g.b0_r = take(kDB0n); g.b0_t = take(kDB0h); g.b0_p = take(kDB0h);
+    g.jp_r = take(kDJp); g.jp_t = take(kDJp); g.jp_p = take(kDJp);
+    g.bh_r = take(kDBh); g.bh_t = take(kDBh); g.bh_p = take(kDBh);
+    g.e1_r = take(kDEnr); g.e1_t = take(kDEnn); g.e1_p = take(kDEnn);
+    g.d_r = take(kDD); g.d_t = take(kDD); g.d_p = take(kDD);
+    g.ec_r = take(kDEc); g.ec_t = take(kDEc); g.ec_p = take(kDEc);
+    uintptr_t a = reinterpret_cast<uintptr_t>(q);
+    a = (a + 15) & ~uintptr_t(15);
+    g.psi = reinterpret_cast<P *>(a);
+  }
+  // ring accessors: (array, depth, row, column offset)
+  auto at = [&](R *ring, int depth, int row, int dc) -> R & { return ring[rs(row, depth) * NC + c + dc]; };
+  const Fields<R> &f = p.f;
+  const Tables<R> &t = p.t;
+  const R dt = p.dt, fp = R(4.0 * kPi) * p.dt;
+  const bool lit = p.ff_interp_e != 0, filt = p.ff_sigma16 != R(0);
+  bool clamped_any = false;
+  unsigned long long nclamp = 0;
+  for (int k = k0; k <= k1; ++k) {
+    // ---------------------------------------------------------------- load
+    if (k <= nr) {
+      const int64_t kn = ix(k, j, n1), kh = ix(k, j, nt);
+      at(g.en_t, kDEn, k, 0) = jh ? src(1, f.et, nt, k) : R(0);
+      at(g.en_p, kDEn, k, 0) = jn ? src(2, f.ep, n1, k) : R(0);
+      at(g.b0_r, kDB0n, k, 0) = jh ? f.br0[kh] : R(0);
+      at(g.bh_r, kDBh, k, 0) = jh ? src(3, f.br, nt, k) : R(0);  // dB_r^n, advanced in place by F1 below
+      at(g.jp_r, kDJp, k, 0) = jn ? f.jpr[kn] : R(0);
+      at(g.jp_t, kDJp, k, 0) = jn ? f.jpt[kn] : R(0);
+      at(g.jp_p, kDJp, k, 0) = jn ? f.jpp[kn] : R(0);
+      g.psi[rs(k, kDPsi) * NC + c] = jn ? f.psi[kn] : P{};
+      if (k < nr) {
+        at(g.en_r, kDEn, k, 0) = jn ? src(0, f.er, n1, k) : R(0);
+        at(g.dbn_t, kDEn, k, 0) = jn ? src(4, f.bt, n1, k) : R(0);
+        at(g.dbn_p, kDEn, k, 0) = jh ? src(5, f.bp, nt, k) : R(0);
+        at(g.b0_t, kDB0h, k, 0) = jn ? f.bt0[kn] : R(0);
+        at(g.b0_p, kDB0h, k, 0) = jh ? f.bp0[kh] : R(0);
+      }
+    }
+    __syncthreads();
+    // ------------------------------------------------------------------ F1
+    if (k <= nr && jh && c < NC - 1) {  // B_r(k, j+1/2)
+      const R cu = t.inv_rn[k] * (t.sn[j + 1] * at(g.en_p, kDEn, k, 1) - t.sn[j] * at(g.en_p, kDEn, k, 0)) *
+                   t.inv_dcp[j];
+      at(g.bh_r, kDBh, k, 0) -= hdt * cu;
+    }
+    if (k >= 1 && k - 1 < nr) {
+      const int i = k - 1;
+      R v = R(0);  // B_th(i+1/2, j): zero on the axis
+      if (j > 0 && j < nt)
+        v = at(g.dbn_t, kDEn, i, 0) +
+            hdt * t.c_b2[i] * (t.rn[i + 1] * at(g.en_p, kDEn, i + 1, 0) - t.rn[i] * at(g.en_p, kDEn, i, 0));
+      at(g.bh_t, kDBh, i, 0) = v;
+      if (jh && c < NC - 1) {  // B_ph(i+1/2, j+1/2)
+        const R cu = t.c_b2[i] * (t.rn[i + 1] * at(g.en_t, kDEn, i + 1, 0) - t.rn[i] * at(g.en_t, kDEn, i, 0)) -
+                     t.c_bp2[i] * (at(g.en_r, kDEn, i, 1) - at(g.en_r, kDEn, i, 0));
+        at(g.bh_p, kDBh, i, 0) = at(g.dbn_p, kDEn, i, 0) - hdt * cu;
+      }
+    }
+    __syncthreads();
+    // ------------------------------------------------------------------- A
+    if (k >= 1 && k - 1 <= nr && c >= 1 && c < NC - 1) {
+      const int i = k - 1;
+      auto psi_at = [&](int row, int dc) { return g.psi[rs(row, kDPsi) * NC + c + dc]; };
+      if (i < nr && jn) {  // E_r(i+1/2, j)
+        R cu = R(0);
+        if (j < nt) cu += t.sh[j] * at(g.bh_p, kDBh, i, 0);
+        if (j > 0) cu -= t.sh[j - 1] * at(g.bh_p, kDBh, i, -1);
+        cu *= t.inv_rh[i] * t.inv_dch[j];
+        const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i + 1, 0)));
+        const bool lo = i >= 1, hi = i + 1 <= nr - 1;
+        R jm = R(0);
+        if (lo) jm += at(g.jp_r, kDJp, i, 0);
+        if (hi) jm += at(g.jp_r, kDJp, i + 1, 0);
+        if (lo && hi) jm *= R(0.5);
+        const int64_t kk = ix(i, j, n1);
+        const R jt = (R(1) - fb) * f.jr[kk] + fb * jm;
+        at(g.e1_r, kDEnr, i, 0) = (at(g.en_r, kDEn, i, 0) + dt * (cu + f.sr[kk]) - fp * jt) * (R(1) - t.sig_h[i]);
+      }
+      if (jh) {  // E_th(i, j+1/2)
+        const int64_t kk = ix(i, j, nt);
+        R v;
+        if (i == 0) {
+          v = -p.omega * t.rn[0] * t.sh[j] * (at(g.b0_r, kDB0n, 0, 0) + at(g.bh_r, kDBh, 0, 0));
+        } else if (i == nr) {
+          v = R(0);
+        } else {
+          const R cu = -t.c_e2[i] * (t.rh[i] * at(g.bh_p, kDBh, i, 0) - t.rh[i - 1] * at(g.bh_p, kDBh, i - 1, 0));
+          const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i, 1)));
+          const R jt = (R(1) - fb) * f.jt[kk] + fb * R(0.5) * (at(g.jp_t, kDJp, i, 0) + at(g.jp_t, kDJp, i, 1));
+          v = (at(g.en_t, kDEn, i, 0) + dt * (cu + f.st[kk]) - fp * jt) * (R(1) - t.sig_n[i]);
+        }
+        at(g.e1_t, kDEnn, i, 0) = v;
+      }
+      if (jn) {  // E_ph(i, j)
+        const int64_t kk = ix(i, j, n1);
+        R v = R(0);
+        if (i >= 1 && i < nr && j >= 1 && j < nt) {
+          const R cu = t.c_e2[i] * (t.rh[i] * at(g.bh_t, kDBh, i, 0) - t.rh[i - 1] * at(g.bh_t, kDBh, i - 1, 0)) -
+                       t.c_ep2[i] * (at(g.bh_r, kDBh, i, 0) - at(g.bh_r, kDBh, i, -1));
+          const R fb = blend(p, psi_at(i, 0));
+          const R jt = (R(1) - fb) * f.jp[kk] + fb * at(g.jp_p, kDJp, i, 0);
+          v = (at(g.en_p, kDEn, i, 0) + dt * (cu + f.sp[kk]) - fp * jt) * (R(1) - t.sig_n[i]);
+        }
+        at(g.e1_p, kDEnn, i, 0) = v;
+      }
+    }
+    __syncthreads();
+    // ------------------------------------------------------------------- N
+    if (k >= 1 && k - 1 <= nr && c >= 1 && c < NC - 1) {
+      const int i = k - 1;
+      R d0 = 0, d1 = 0, d2 = 0;
+      if (i >= 1 && i < nr && jn) {
+        const bool axis = (j == 0 || j == nt);
+        R e[3], b[3];
+        e[0] = R(0.5) * (at(g.e1_r, kDEnr, i - 1, 0) + at(g.e1_r, kDEnr, i, 0));
+        e[1] = axis ? R(0) : R(0.5) * (at(g.e1_t, kDEnn, i, -1) + at(g.e1_t, kDEnn, i, 0));
+        e[2] = axis ? R(0) : at(g.e1_p, kDEnn, i, 0);
+        auto br = [&](int dc) { return at(g.b0_r, kDB0n, i, dc) + at(g.bh_r, kDBh, i, dc); };
+        auto bt = [&](int row) { return at(g.b0_t, kDB0h, row, 0) + at(g.bh_t, kDBh, row, 0); };
+        auto bp = [&](int row, int dc) { return at(g.b0_p, kDB0h, row, dc) + at(g.bh_p, kDBh, row, dc); };
+        b[0] = (j == 0) ? br(0) : (j == nt) ? br(-1) : R(0.5) * (br(-1) + br(0));
+        b[1] = axis ? R(0) : R(0.5) * (bt(i - 1) + bt(i));
+        b[2] = axis ? R(0) : R(0.25) * (bp(i - 1, -1) + bp(i - 1, 0) + bp(i, -1) + bp(i, 0));
+        const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        if (b2 > b2min<R>()) {
+          const R sdot = (e[0] * b[0] + e[1] * b[1] + e[2] * b[2]) / b2;
+          const R x = e[0] - sdot * b[0], y = e[1] - sdot * b[1], z = e[2] - sdot * b[2];
+          const R e2 = x * x + y * y + z * z;
+          const R sc = (e2 > b2) ? sqrt(b2 / e2) : R(1);
+          d0 = sc * x - e[0];
+          d1 = sc * y - e[1];
+          d2 = sc * z - e[2];
+          if (e2 > b2 && own && i >= i_s && i < i_e) { clamped_any = true; ++nclamp; }
+        }
+        if (lit) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
+      }
+      at(g.d_r, kDD, i, 0) = d0;
+      at(g.d_t, kDD, i, 0) = d1;
+      at(g.d_p, kDD, i, 0) = d2;
+      if (own && jn && i >= i_s && i < i_e) {
+        const int64_t kk = ix(i, j, n1);
+        f.der[kk] = d0; f.det[kk] = d1; f.dep[kk] = d2;
+      }
+    }
+    __syncthreads();
+    // ------------------------------------------------------------------- C
+    if (k >= 3 && k - 3 <= nr && c >= 2 && c < NC - 2) {
+      const int i = k - 3;
+      auto psi_at = [&](int row, int dc) { return g.psi[rs(row, kDPsi) * NC + c + dc]; };
+      if (i < nr && jn) {  // E_r(i+1/2, j)
+        R v = at(g.e1_r, kDEnr, i, 0);
+        const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i + 1, 0)));
+        if (fb != R(0)) {
+          const bool lo = i >= 1, hi = i + 1 <= nr - 1;
+          R m = R(0);
+          if (lo) m += at(g.d_r, kDD, i, 0);
+          if (hi) m += at(g.d_r, kDD, i + 1, 0);
+          if (lo && hi) m *= R(0.5);
+          if (filt && i >= 2 && i <= nr - 3)
+            m -= p.ff_sigma16 * (at(g.e1_r, kDEnr, i - 2, 0) - R(4) * at(g.e1_r, kDEnr, i - 1, 0) + R(6) * v -
+                                 R(4) * at(g.e1_r, kDEnr, i + 1, 0) + at(g.e1_r, kDEnr, i + 2, 0));
+          v += fb * (lit ? m - v : m);
+        }
+        at(g.ec_r, kDEc, i, 0) = v;
+        if (own && i >= i_s && i < i_e) f.er[ix(i, j, n1)] = v;
+      }
+      if (jh) {  // E_th(i, j+1/2)
+        R v = at(g.e1_t, kDEnn, i, 0);
+        if (i >= 1 && i < nr) {
+          const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i, 1)));
+          if (fb != R(0)) {
+            R m = R(0.5) * (at(g.d_t, kDD, i, 0) + at(g.d_t, kDD, i, 1));
+            if (filt && j >= 2 && j <= nt - 3)
+              m -= p.ff_sigma16 * (at(g.e1_t, kDEnn, i, -2) - R(4) * at(g.e1_t, kDEnn, i, -1) + R(6) * v -
+                                   R(4) * at(g.e1_t, kDEnn, i, 1) + at(g.e1_t, kDEnn, i, 2));
+            v += fb * (lit ? m - v : m);
+          }
+        }
+        at(g.ec_t, kDEc, i, 0) = v;
+        if (own && i >= i_s && i < i_e) f.et[ix(i, j, nt)] = v;
+      }
+      if (jn) {  // E_ph(i, j)
+        R v = at(g.e1_p, kDEnn, i, 0);
+        if (i >= 1 && i < nr && j >= 1 && j < nt) {
+          const R fb = blend(p, psi_at(i, 0));
+          if (fb != R(0)) {
+            const R m = at(g.d_p, kDD, i, 0);
+            v += fb * (lit ? m - v : m);
+          }
+        }
+        at(g.ec_p, kDEc, i, 0) = v;
+        if (own && i >= i_s && i < i_e) f.ep[ix(i, j, n1)] = v;
+      }
+    }
+    __syncthreads();
+    // ------------------------------------------------------------------ F2
+    if (own) {
+      if (k >= 3 && k - 3 <= nr && jh) {  // B_r(i, j+1/2), i = k-3
+        const int i = k - 3;
+        const R cu = t.inv_rn[i] * (t.sn[j + 1] * at(g.ec_p, kDEc, i, 1) - t.sn[j] * at(g.ec_p, kDEc, i, 0)) *
+                     t.inv_dcp[j];
+        R v = at(g.bh_r, kDBh, i, 0) - hdt * cu;
+        const R sg = t.sig_n[i];
+        if (sg > R(0)) v -= sg * v;
+        if (i >= i_s && i < i_e) f.br[ix(i, j, nt)] = v;
+      }
+      if (k >= 4 && k - 4 < nr) {  // B_th, B_ph at half row i = k-4
+        const int i = k - 4;
+        if (i >= i_s && i < i_e) {
+          if (jn) {
+            R v = R(0);
+            if (j > 0 && j < nt) {
+              v = at(g.bh_t, kDBh, i, 0) +
+                  hdt * t.c_b2[i] * (t.rn[i + 1] * at(g.ec_p, kDEc, i + 1, 0) - t.rn[i] * at(g.ec_p, kDEc, i, 0));
+              const R sg = t.sig_h[i];
+              if (sg > R(0)) v -= sg * v;
+            }
+            f.bt[ix(i, j, n1)] = v;
+          }
+          if (jh) {
+            const R cu = t.c_b2[i] * (t.rn[i + 1] * at(g.ec_t, kDEc, i + 1, 0) - t.rn[i] * at(g.ec_t, kDEc, i, 0)) -
+                         t.c_bp2[i] * (at(g.ec_r, kDEc, i, 1) - at(g.ec_r, kDEc, i, 0));
+            R w = at(g.bh_p, kDBh, i, 0) - hdt * cu;
+            const R sg = t.sig_h[i];
+            if (sg > R(0)) w -= sg * w;
+            f.bp[ix(i, j, nt)] = w;
+          }
+        }
+      }
+    }
+    __syncthreads();  // the next step's loads reuse ring slots
+  }
+  // running count of Eq. 26 activations (see k_node_b)
+  const unsigned m = __ballot_sync(0xffffffffu, clamped_any);
+  unsigned long long tot = nclamp;
+  for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+  if (m && (threadIdx.x & 31) == 0 && tot) atomicAdd(p.clamps, tot);
+}
+
+template <typename R> size_t field_fused_smem() { return fuse_smem_bytes<R>(); }
+template <typename R> const void *field_fused_fn() { return reinterpret_cast<const void *>(&k_field_fused<R>); }
+template <typename R> cudaError_t set_field_fused_smem(size_t bytes) { return raise_smem_limit<field_fused_fn<R>>(bytes); }
+// rows per segment: enough blocks for the GPU (about eight per SM), at
+// least 32 rows so that the warm-up stays a small share
+int fuse_seg_rows(int nr, int nt, int n_sm) {
+  const int strips = (nt + 1 + kFuseOwn - 1) / kFuseOwn;
+  const int want = std::max(1, (8 * n_sm + strips - 1) / strips);
+  return std::max(32, (nr + 1 + want - 1) / want);
+}
+size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real) {
+  const FuseGeom fg = fuse_geom(nr, nt, seg_rows);
+  return (size_t)(fuse_snap_cols(nr, fg.strips) + fuse_snap_rows(nt, fg.segs)) * real;
+}
+template <typename R> void launch_field_fused(const Params<R> &p, int seg_rows, void *snap, cudaStream_t s) {
+  const FuseGeom fg = fuse_geom(p.nr, p.nt, seg_rows);
+  R *sc = reinterpret_cast<R *>(snap);
+  R *sr = sc + fuse_snap_cols(p.nr, fg.strips);
+  const int64_t n = fuse_snap_cols(p.nr, fg.strips) + fuse_snap_rows(p.nt, fg.segs);
+  if (n > 0) k_fuse_snap<R><<<(unsigned)std::min<int64_t>((n + 255) / 256, 16384), 256, 0, s>>>(p, sc, sr, fg);
+  k_field_fused<R><<<dim3(fg.strips, fg.segs), kFuseThreads, fuse_smem_bytes<R>(), s>>>(p, R(0.5) * p.dt, fg, sc, sr);
+}
+
 // The blend weights of the last flux prefix, on request (hff_fields): f at
 // the E_r and E_th edges and at the nodes, and the force-free cell flags
 // (outputs passed as null are skipped).
@@ -457,7 +881,10 @@ template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
   template void launch_correct<R>(const Params<R> &, cudaStream_t);            \
-  template void launch_blend_out<R>(const Params<R> &, R *, R *, R *, uint8_t *, cudaStream_t);
+  template void launch_blend_out<R>(const Params<R> &, R *, R *, R *, uint8_t *, cudaStream_t); \
+  template void launch_field_fused<R>(const Params<R> &, int, void *, cudaStream_t);            \
+  template size_t field_fused_smem<R>();                                                         \
+  template cudaError_t set_field_fused_smem<R>(size_t);
 HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST

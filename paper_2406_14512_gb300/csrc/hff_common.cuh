@@ -243,6 +243,14 @@ template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
 // f at the E_r edges, E_th edges and nodes, and the force-free cell flags,
 // from the current Psi (on request)
 template <typename R> void launch_blend_out(const Params<R> &p, R *fr, R *ft, R *fn, uint8_t *cells, cudaStream_t s);
+// the whole field update between the push and the injection (Faraday half,
+// Ampere, renormalisation, return, Faraday half with absorber) in one pass
+// over row segments of seg_rows rows
+template <typename R> void launch_field_fused(const Params<R> &p, int seg_rows, void *snap, cudaStream_t s);
+int fuse_seg_rows(int nr, int nt, int n_sm);                        // rows per segment of the launch
+size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real);  // its halo snapshot
+template <typename R> size_t field_fused_smem();
+template <typename R> cudaError_t set_field_fused_smem(size_t bytes);
 // dst[k] = a[k] + sign * b[k], k < n (B <-> B - B_0 at the ABI)
 template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_t n, int sign, cudaStream_t s);
 
