@@ -336,6 +336,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--tile", default=None, help="tile_r x tile_t of the sort and the tiled push, e.g. 16x24")
     ap.add_argument("--sort-every", type=int, default=None)
+    ap.add_argument("--field-pass", type=int, default=None, choices=[0, 1],
+                    help="field update: 0 = one fused pass (the default), 1 = four kernels")
     ap.add_argument("--oracle-sample", default="128", choices=["128", "full"],
                     help="reference arm: time the oracle on a 128^2 sample (default) or the full workload")
     ap.add_argument("--ensemble-mode", default="graph", choices=["graph", "sequential"],
@@ -376,6 +378,8 @@ def main():
         cfg["tile_r"], cfg["tile_t"] = (int(x) for x in args.tile.lower().split("x"))
     if args.sort_every:
         cfg["sort_every"] = args.sort_every
+    if args.field_pass is not None:
+        cfg["field_pass"] = args.field_pass
     cfg["seed"] = int(cfg["seed"]) + 1000 * rank
     cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
     prec = cfg.get("precision", "fp32")
@@ -551,6 +555,7 @@ def main():
             "cells": cells,
             "sort_every": cfg["sort_every"],
             "tile": [cfg["tile_r"], cfg["tile_t"]],
+            "field_pass": int(cfg.get("field_pass", hff.FIELD_PASS_DEFAULT)),
             "launch_shape": tuned or "configured",
             "l2": "inputs larger than L2 (particle state %.1f GB)" % (n_live0 * (28 if prec == "fp32" else 52) / 1e9),
             "parallelism": "replicas" if ws > 1 else "single",

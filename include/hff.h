@@ -87,8 +87,14 @@ extern "C" {
 #define HFF_HOST 0
 #define HFF_DEVICE 1
 
+/* hff_config.field_pass */
+#define HFF_FIELDS_FUSED 0
+#define HFF_FIELDS_SPLIT 1
+
 /* stage bits of hff_step_stages (a full step runs all, in this order) */
-#define HFF_ST_NODE 1      /* Psi, J_perp, per-cell force-free flag              */
+#define HFF_ST_NODE 1      /* Psi, per-cell force-free flag; J_perp here unless
+                              the fused field pass (with all four field stages
+                              in the same call) computes it                 */
 #define HFF_ST_CORRECT 2   /* Delta E at the nodes and E += f <Delta E>          */
 #define HFF_ST_PUSH 4      /* push, move, deposit                               */
 #define HFF_ST_FARADAY1 8  /* B^n -> B^{n+1/2}                                  */
@@ -169,6 +175,17 @@ typedef struct hff_config {
                                node corrections cannot act on it; sigma = 1
                                removes it, and a smooth field changes by O(h^4)
                                per step.  0 = off (a reading: the paper is silent) */
+  int32_t field_pass;       /* how the field update runs (the results agree to
+                               rounding): HFF_FIELDS_FUSED (0) = one
+                               row-pipelined pass over theta strips and row
+                               segments after the push, which computes J_perp
+                               itself and reads E and dB once (it needs a halo
+                               snapshot of E and dB, about 15% of their size
+                               on a 4096^2 grid); HFF_FIELDS_SPLIT (1) = J_perp
+                               at the nodes before the push, then four kernels
+                               after it (Faraday half step, Ampere,
+                               renormalisation and return, Faraday half step
+                               with the absorber)                               */
 } hff_config;
 
 typedef struct hff_info {

@@ -138,6 +138,8 @@ int validate(const hff_config *c) {
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
   if (!(c->ff_filter >= 0.0 && c->ff_filter <= 1.0)) return fail(HFF_ERR_ARG, "ff_filter must be in [0, 1]");
+  if (c->field_pass != HFF_FIELDS_FUSED && c->field_pass != HFF_FIELDS_SPLIT)
+    return fail(HFF_ERR_ARG, "field_pass must be HFF_FIELDS_FUSED or HFF_FIELDS_SPLIT");
   if (c->inject_species[0] != c->inject_species[1])
     for (int k = 0; k < 2; ++k)
       if (c->inject_species[k] < 0 || c->inject_species[k] >= c->n_species)
@@ -254,10 +256,12 @@ void layout(const hff_config &c, Offsets &o) {
   o.qnode = L.take(nn * 8);
   o.rows = L.take((nr + 1) * 8 * 8);
   o.psi64 = L.take(nn * 8);
-  // the fused field update's segments are sized for the 152 SMs of a GB300
-  // (a property of the grid, not of the device, so that hff_plan needs no GPU)
-  o.seg_rows = fuse_seg_rows(c.nr, c.nt, 152);
-  o.fsnap = L.take(fuse_snap_bytes(c.nr, c.nt, o.seg_rows, R));
+  // the fused field update's snapshot is sized for its shortest segments:
+  // one wave of up to eight blocks on each of the 152 SMs of a GB300 (a
+  // property of the grid, not of the device, so that hff_plan needs no GPU);
+  // hff_init lengthens them to the measured occupancy
+  o.seg_rows = fuse_seg_rows(c.nr, c.nt, 152 * 8);
+  o.fsnap = c.field_pass == HFF_FIELDS_FUSED ? L.take(fuse_snap_bytes(c.nr, c.nt, o.seg_rows, R)) : 0;
   o.total = (L.off + 255) & ~size_t(255);
 }
 
@@ -272,6 +276,7 @@ struct hff_handle {
   Geom g;
   double dt = 0, psi_unit = 0, xi_abs = 0;
   int halo = 0, push_grid = 0, tail_grid = 0;
+  int seg_rows = 0;  // rows per segment of the fused field update (>= o.seg_rows)
   Params<float> pf[2];
   Params<double> pd[2];
   WorkList wl{};
@@ -608,9 +613,13 @@ int init_state(hff_handle *h) {
 template <typename R>
 int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts = 7, bool gather = false) {
   Params<R> &p = params<R>(h)[par];
+  constexpr int kFieldStages = HFF_ST_FARADAY1 | HFF_ST_AMPERE | HFF_ST_CORRECT | HFF_ST_FARADAY2;
+  // the fused field update computes J_perp itself from E^n, B^n
+  const bool fused = h->c.field_pass == HFF_FIELDS_FUSED && (stages & kFieldStages) == kFieldStages;
   if ((parts & 1) && (stages & HFF_ST_NODE)) {
     launch_psi<R>(p, s);
-    launch_node_a<R>(p, s);
+    if (fused) launch_ffcell<R>(p, s);
+    else launch_node_a<R>(p, s);
   }
   if ((parts & 1) && (stages & HFF_ST_PUSH) && h->c.sort_every > 0)
     CK(cudaMemsetAsync(&h->small->next, 0, sizeof(int), s));
@@ -623,10 +632,9 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
     return HFF_OK;
   }
   if (stages & HFF_ST_PUSH) launch_push_tail<R>(p, s, h->tail_grid);
-  constexpr int kFieldStages = HFF_ST_FARADAY1 | HFF_ST_AMPERE | HFF_ST_CORRECT | HFF_ST_FARADAY2;
-  if ((stages & kFieldStages) == kFieldStages) {
+  if (fused) {
     // the whole field update in one pass; J_PIC cleared for the next deposit
-    launch_field_fused<R>(p, h->o.seg_rows, h->base + h->o.fsnap, s);
+    launch_field_fused<R>(p, h->seg_rows, h->base + h->o.fsnap, s);
     const int64_t nr = h->c.nr, nt = h->c.nt;
     CK(cudaMemsetAsync(p.f.jr, 0, (size_t)(nr * (nt + 1)) * sizeof(R), s));
     CK(cudaMemsetAsync(p.f.jt, 0, (size_t)((nr + 1) * nt) * sizeof(R), s));
@@ -1110,6 +1118,9 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
     const cudaError_t e2 = cfg->precision == HFF_FP64 ? set_field_fused_smem<double>(field_fused_smem<double>())
                                                       : set_field_fused_smem<float>(field_fused_smem<float>());
     if (e2 != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the fused field update's shared memory size"));
+    // one wave of the fused field update at its occupancy on this device
+    const int occ = cfg->precision == HFF_FP64 ? field_fused_blocks_per_sm<double>() : field_fused_blocks_per_sm<float>();
+    h->seg_rows = std::max(h->o.seg_rows, fuse_seg_rows(cfg->nr, cfg->nt, std::max(1, occ) * nsm));
   }
   if (cfg->precision == HFF_FP32) {
     fill_params<float>(h);

@@ -14,6 +14,7 @@
 // |B|: near the star of a fine grid the rounding of a stored |B| ~ 1, divided
 // by a cell of 1e-3 r*, would otherwise enter E every step through the curl.
 #include <algorithm>
+#include <type_traits>
 
 #include "hff_common.cuh"
 
@@ -399,57 +400,64 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
 }
 
 // ------------------------------------------------------- fused field update
-// The field update between the push and the injection -- Faraday's first
-// half step (Eq. 18), Ampere's law with the blended current (Eqs. 19, 28) and
-// the boundaries, the renormalisation at the nodes (Eqs. 25-26), the return to
+// The field update between the push and the injection -- J_perp at the
+// nodes from E^n, B^n (first term of Eq. 24), Faraday's first half step
+// (Eq. 18), Ampere's law with the blended current (Eqs. 19, 28) and the
+// boundaries, the renormalisation at the nodes (Eqs. 25-26), the return to
 // the edges with the blend weights, and Faraday's second half step with the
-// absorber -- as one pass.  A block owns a strip of theta columns (with a
-// halo of kFuseHalo columns on each side, recomputed) and a segment of rows
-// (with kFuseWarm rows of warm-up below it, recomputed), and walks the rows
-// upward.  At row step k it loads node row k and half row k (k+1/2) of E^n,
-// dB^n, B_0, J_perp and Psi into ring buffers in shared memory, and then:
-//   F1: B^{n+1/2} at node row k (B_r) and half row k-1 (B_th, B_ph);
-//   A : E^{n+1} at half row k-1 (E_r) and node row k-1 (E_th, E_ph), J cleared;
-//   N : Delta E (or E'') at node row k-1, and the filter terms;
-//   C : the corrected E at half row k-3 and node row k-3;
-//   F2: dB^{n+1} at node row k-3 (B_r) and half row k-4 (B_th, B_ph).
-// Each stage reads only rows the earlier stages of this or previous steps
-// produced, so every value is computed once per block from E^n and dB^n read
-// once; the outputs are written once.  The arithmetic is that of k_faraday,
-// k_ampere, k_node_b and k_correct, location by location.
+// absorber -- as one pass.  A block owns a strip of theta columns (with
+// kFuseHalo columns recomputed on each side) and a segment of rows (with
+// kFuseWarm rows of warm-up below it), and walks the rows upward.  Row step
+// k has four phases separated by barriers:
+//   0: F2, dB^{n+1} at node row k-4 (B_r) and half row k-5 (B_th, B_ph);
+//      node row k and half row k (k+1/2) of E^n, dB^n, B_0, Psi and the
+//      radial tables, loaded one step earlier, go to shared-memory rings,
+//      and the loads of row k+1 are issued (they complete behind phases
+//      1-3);
+//   1: F1, B^{n+1/2} at node row k (B_r) and half row k-1 (B_th, B_ph), and
+//      J_perp at node row k;
+//   2: A, E^{n+1} at half row k-1 (E_r) and node row k-1 (E_th, E_ph), with
+//      the blend weights f kept in registers for phase 3 two steps later;
+//      N, Delta E (or E'') at node row k-2, and the filter terms;
+//   3: C, the corrected E at half row k-3 and node row k-3.
+// Every stage reads only what earlier phases produced, so E^n and dB^n are
+// read once and every output written once; the arithmetic is that of
+// k_node_a, k_faraday, k_ampere, k_node_b and k_correct, location by
+// location.  Column and row ranges: F2 needs the corrected E at columns c,
+// c+1; C (with the theta filter) the uncorrected E at c-2 .. c+2 and Delta E
+// at c, c+1; N and A one column to the left, F1 and J_perp one more on
+// either side, so three columns of halo suffice on each side, and likewise
+// three rows of warm-up (C's radial filter reaches two rows down, A and F1
+// one more each).
 //
 // The update is in place, and a block's halo columns and warm-up / trailing
 // rows belong to its neighbours, which overwrite them during the same
 // launch; so a block reads E^n and dB^n live only inside its own area (which
 // no other block writes, and which it overwrites only rows below the one it
 // is reading), and everywhere else from a snapshot of those regions taken
-// just before (k_fuse_snap).  J_PIC, read inside the halos too, is cleared by
-// the caller after the launch.
+// just before (k_fuse_snap_cols, k_fuse_snap_rows).  J_PIC is only read, and
+// the caller clears it after the launch.
 constexpr int kFuseThreads = 128;     // columns of a strip, halo included
-constexpr int kFuseHalo = 8;          // columns recomputed on each side
-constexpr int kFuseWarm = 8;          // rows recomputed below a segment
-// ring depths (rows live at once, see the step order above)
-constexpr int kDEn = 2, kDBh = 4, kDB0n = 2, kDB0h = 3, kDJp = 2, kDPsi = 4, kDEnr = 5, kDEnn = 3, kDD = 3,
-              kDEc = 2;
-
-template <typename R>
-struct FuseRings {
-  R *en_r, *en_t, *en_p;        // E^n            (half, node, node)   kDEn
-  R *dbn_t, *dbn_p;             // dB^n           (half, half)         kDEn
-  R *b0_r, *b0_t, *b0_p;        // B_0            (node, half, half)   kDB0n, kDB0h
-  R *jp_r, *jp_t, *jp_p;        // J_perp         (node)               kDJp
-  typename PsiOf<R>::T *psi;    // Psi            (node)               kDPsi
-  R *bh_r, *bh_t, *bh_p;        // dB^{n+1/2}     (node, half, half)   kDBh
-  R *e1_r, *e1_t, *e1_p;        // E^{n+1} before the correction (half kDEnr, node kDEnn)
-  R *d_r, *d_t, *d_p;           // Delta E or E'' (node)               kDD
-  R *ec_r, *ec_t, *ec_p;        // corrected E    (half, node, node)   kDEc
-};
+constexpr int kFuseHalo = 4;          // columns recomputed on each side
+constexpr int kFuseWarm = 4;          // rows recomputed below a segment
+constexpr int kFuseTrail = 5;         // rows above a segment the pipeline loads (up to i_e + 3)
+constexpr int kFuseOwn = kFuseThreads - 2 * kFuseHalo;
+constexpr int kFuseArrays = 6;        // E_r E_th E_ph dB_r dB_th dB_ph
+// ring depths: rows live at once (see the phase order above)
+constexpr int kDEn = 2, kDDbr = 1, kDDbn = 2, kDB0r = 3, kDB0h = 4, kDJp = 2, kDPsi = 2, kDBr = 4, kDBh = 4,
+              kDE1r = 5, kDE1n = 3, kDD = 2, kDEc = 2, kDTab = 8;
+constexpr int kFuseRingRows = 3 * kDEn + kDDbr + 2 * kDDbn + kDB0r + 2 * kDB0h + 3 * kDJp + kDBr + 2 * kDBh + kDE1r +
+                              2 * kDE1n + 3 * kDD + 3 * kDEc;
+// radial tables of a row, staged in shared memory by the first threads
+enum FuseTab { TB_RN, TB_INV_RN, TB_C_E2, TB_C_EP2, TB_SIG_N, TB_RHO_A, TB_RHO_B, TB_RH, TB_INV_RH, TB_C_B2,
+               TB_C_BP2, TB_SIG_H, TB_RH2, TB_COUNT };
+constexpr int kTabN = 16;
+static_assert(TB_COUNT <= kTabN && TB_COUNT <= kFuseThreads, "table row");
 
 template <typename R>
 size_t fuse_smem_bytes() {
-  const size_t rows = 3 * kDEn + 2 * kDEn + kDB0n + 2 * kDB0h + 3 * kDJp + 3 * kDBh + kDEnr + 2 * kDEnn + 3 * kDD +
-                      3 * kDEc;
-  return rows * kFuseThreads * sizeof(R) + (size_t)kDPsi * kFuseThreads * sizeof(typename PsiOf<R>::T) + 64;
+  return ((size_t)kFuseRingRows * kFuseThreads + (size_t)kDTab * kTabN) * sizeof(R) +
+         (size_t)kDPsi * kFuseThreads * sizeof(typename PsiOf<R>::T) + 16;
 }
 
 // Geometry of a launch: strips of kFuseOwn owned columns, segments of
@@ -458,9 +466,6 @@ size_t fuse_smem_bytes() {
 // the 2 kFuseHalo columns around column b kFuseOwn over all rows, and for
 // every segment boundary b = 1 .. segs-1 the rows from b seg_rows - kFuseWarm
 // to b seg_rows + kFuseTrail - 1 over all columns.
-constexpr int kFuseOwn = kFuseThreads - 2 * kFuseHalo;
-constexpr int kFuseTrail = 5;   // rows above a segment the pipeline reads (k1 = i_e + 4)
-constexpr int kFuseArrays = 6;  // E_r E_th E_ph dB_r dB_th dB_ph
 struct FuseGeom {
   int strips, segs, seg_rows;
 };
@@ -491,193 +496,354 @@ __device__ __forceinline__ const R *fuse_array(const Params<R> &p, int a, int &l
   }
 }
 
-// the snapshot (one thread per snapshot element)
+// the snapshot: halo columns (block 2 kFuseHalo x 32: column, row) ...
 template <typename R>
-__global__ void k_fuse_snap(Params<R> p, R *snap_c, R *snap_r, FuseGeom fg) {
-  const int nr = p.nr, nt = p.nt;
-  const int64_t nc = fuse_snap_cols(nr, fg.strips), nrw = fuse_snap_rows(nt, fg.segs);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc + nrw; e += (int64_t)gridDim.x * blockDim.x) {
-    int b, a, row, col;
-    if (e < nc) {
-      const int w = 2 * kFuseHalo;
-      int64_t q = e;
-      const int cc = (int)(q % w); q /= w;
-      row = (int)(q % (nr + 1)); q /= (nr + 1);
-      a = (int)(q % kFuseArrays); b = (int)(q / kFuseArrays) + 1;
-      col = b * kFuseOwn - kFuseHalo + cc;
-    } else {
-      const int h = kFuseWarm + kFuseTrail;
-      int64_t q = e - nc;
-      col = (int)(q % (nt + 1)); q /= (nt + 1);
-      const int rr = (int)(q % h); q /= h;
-      a = (int)(q % kFuseArrays); b = (int)(q / kFuseArrays) + 1;
-      row = b * fg.seg_rows - kFuseWarm + rr;
-    }
-    int ld, rows, cols;
-    const R *src = fuse_array(p, a, ld, rows, cols);
-    const R v = (row >= 0 && row < rows && col >= 0 && col < cols) ? src[(int64_t)row * ld + col] : R(0);
-    if (e < nc) snap_c[e] = v;
-    else snap_r[e - nc] = v;
-  }
+__global__ void k_fuse_snap_cols(Params<R> p, R *snap_c) {
+  const int cc = threadIdx.x, row = blockIdx.x * blockDim.y + threadIdx.y, ba = blockIdx.y;
+  if (row > p.nr) return;
+  const int a = ba % kFuseArrays, b = ba / kFuseArrays + 1;
+  const int col = b * kFuseOwn - kFuseHalo + cc;
+  int ld, rows, cols;
+  const R *src = fuse_array(p, a, ld, rows, cols);
+  const R v = (row < rows && col >= 0 && col < cols) ? src[(int64_t)row * ld + col] : R(0);
+  snap_c[((int64_t)ba * (p.nr + 1) + row) * (2 * kFuseHalo) + cc] = v;
+}
+// ... and warm-up / trailing rows (grid: columns, row of the window, boundary x array)
+template <typename R>
+__global__ void k_fuse_snap_rows(Params<R> p, R *snap_r, int seg_rows) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x, rr = blockIdx.y, ba = blockIdx.z;
+  if (col > p.nt) return;
+  const int a = ba % kFuseArrays, b = ba / kFuseArrays + 1;
+  const int row = b * seg_rows - kFuseWarm + rr;
+  int ld, rows, cols;
+  const R *src = fuse_array(p, a, ld, rows, cols);
+  const R v = (row >= 0 && row < rows && col < cols) ? src[(int64_t)row * ld + col] : R(0);
+  snap_r[((int64_t)ba * (kFuseWarm + kFuseTrail) + rr) * (p.nt + 1) + col] = v;
 }
 
-// ring slot of a row (rows may be negative for never-used slots)
-__device__ __forceinline__ int rs(int row, int depth) { return ((row % depth) + depth) % depth; }
+// a ring of rows in shared memory, one element per column of the strip
+template <typename T, int D>
+struct FRing {
+  T *p;
+  __device__ __forceinline__ T &operator()(int row, int c) const {
+    return p[((unsigned)row % (unsigned)D) * kFuseThreads + c];
+  }
+};
+
+// node row k and half row k of one column, in flight between phase 0 of
+// step k-1 and phase 0 of step k
+template <typename R>
+struct FuseRow {
+  R er, et, ep, br, bt, bp, b0r, b0t, b0p, tab;
+  typename PsiOf<R>::T psi;
+};
+// J_PIC and curl B_0 of one column at the E locations of row k (half row
+// for E_r, node row for E_th and E_ph), used by phase 2 of step k+1
+template <typename R>
+struct FuseSrc {
+  R jr, sr, jt, st, jp, sp;
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kFuseThreads) k_field_fused(Params<R> p, R hdt, FuseGeom fg, const R *snap_c,
                                                               const R *snap_r) {
   using P = typename PsiOf<R>::T;
+  constexpr int NC = kFuseThreads, H = kFuseHalo, W = kFuseWarm;
   extern __shared__ __align__(16) unsigned char fsmem[];
-  const int nr = p.nr, nt = p.nt, n1 = nt + 1, NC = kFuseThreads, seg_rows = fg.seg_rows;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1, seg_rows = fg.seg_rows;
   const int c = threadIdx.x, sx = blockIdx.x, sy = blockIdx.y;
-  const int j = sx * kFuseOwn - kFuseHalo + c;                          // global column of this thread
-  const bool jn = j >= 0 && j <= nt, jh = j >= 0 && j < nt;          // node / half column exists
-  const bool own = c >= kFuseHalo && c < NC - kFuseHalo;               // column written by this block
-  const int i_s = sy * seg_rows;                                       // first output row
+  const int j = sx * kFuseOwn - H + c;                                 // global column of this thread
+  const bool jn = j >= 0 && j <= nt, jh = j >= 0 && j < nt;           // node / half column exists
+  const bool own = c >= H && c < NC - H;                              // column written by this block
+  const int i_s = sy * seg_rows;                                      // first output row
   if (i_s > nr) return;
-  const int i_e = min(i_s + seg_rows, nr + 1);                         // one past the last output node row
-  // E^n and dB^n at (row, column j): live inside this block's own area,
-  // from the snapshot in the halo columns and the warm-up / trailing rows
-  auto src = [&](int a, const R *live, int ld, int row) -> R {
-    if (own && row >= i_s && row < i_e) return live[(int64_t)row * ld + j];
-    if (!own) {
-      const int b = (c < kFuseHalo) ? sx : sx + 1;                     // strip boundary
-      const int cc = j - (b * kFuseOwn - kFuseHalo);
-      return snap_c[(((int64_t)(b - 1) * kFuseArrays + a) * (nr + 1) + row) * (2 * kFuseHalo) + cc];
+  const int i_e = min(i_s + seg_rows, nr + 1);                        // one past the last output node row
+  const int k0 = max(0, i_s - W), kl = min(nr, i_e) + 3;              // row steps with phases 1-3
+  const Fields<R> &f = p.f;
+  const Tables<R> &t = p.t;
+  // snapshot offset of a halo column (array 0, row 0); unused where the
+  // column is outside the grid (the first strip's left and the last
+  // strip's right halo)
+  int64_t sc0 = 0;
+  if (!own) {
+    const int b = (c < H) ? sx : sx + 1;
+    sc0 = (int64_t)(b - 1) * kFuseArrays * (nr + 1) * (2 * H) + (j - (b * kFuseOwn - H));
+  }
+  // the radial table this thread stages (threads 0 .. TB_COUNT-1)
+  const R *tp = nullptr;
+  int tlim = -1;
+  switch (c) {
+    case TB_RN: tp = t.rn; tlim = nr; break;
+    case TB_INV_RN: tp = t.inv_rn; tlim = nr; break;
+    case TB_C_E2: tp = t.c_e2; tlim = nr; break;
+    case TB_C_EP2: tp = t.c_ep2; tlim = nr; break;
+    case TB_SIG_N: tp = t.sig_n; tlim = nr; break;
+    case TB_RHO_A: tp = t.rho_a; tlim = nr; break;
+    case TB_RHO_B: tp = t.rho_b; tlim = nr; break;
+    case TB_RH: tp = t.rh; tlim = nr - 1; break;
+    case TB_INV_RH: tp = t.inv_rh; tlim = nr - 1; break;
+    case TB_C_B2: tp = t.c_b2; tlim = nr - 1; break;
+    case TB_C_BP2: tp = t.c_bp2; tlim = nr - 1; break;
+    case TB_SIG_H: tp = t.sig_h; tlim = nr - 1; break;
+    case TB_RH2: tp = t.rh2; tlim = nr - 1; break;
+    default: break;
+  }
+  // Row steps come in two versions: interior steps, whose rows k-5 .. k+1
+  // all lie inside this block's own rows and inside rows 2 .. nr-3 (every
+  // row condition below holds), and the general one.  IN is true in the
+  // former, where the compiler drops the row conditions.
+  //
+  // E^n and dB^n of node row k and half row k: live inside this block's own
+  // area, from the snapshot in the halo columns and the warm-up / trailing
+  // rows; then B_0, Psi and the radial table of the row
+  auto fetch = [&](int k, FuseRow<R> &x, auto tag) {
+    constexpr bool IN = decltype(tag)::value;
+    const bool node = IN || k <= nr, half = IN || k < nr;
+    const bool cer = half && jn, cet = node && jh, cep = node && jn, cbr = node && jh, cbt = half && jn,
+               cbp = half && jh;
+    const int64_t kn = (int64_t)k * n1 + j, kh = (int64_t)k * nt + j;
+    if (own && (IN || (k >= i_s && k < i_e))) {
+      x.er = cer ? f.er[kn] : R(0);
+      x.et = cet ? f.et[kh] : R(0);
+      x.ep = cep ? f.ep[kn] : R(0);
+      x.br = cbr ? f.br[kh] : R(0);
+      x.bt = cbt ? f.bt[kn] : R(0);
+      x.bp = cbp ? f.bp[kh] : R(0);
+    } else {
+      // array a of the snapshot at s + a as (see k_fuse_snap_rows / _cols)
+      const R *s;
+      int64_t as;
+      if (own) {
+        const int b = (k < i_s) ? sy : sy + 1;
+        s = snap_r + ((int64_t)(b - 1) * kFuseArrays * (W + kFuseTrail) + (k - (b * seg_rows - W))) * n1 + j;
+        as = (int64_t)(W + kFuseTrail) * n1;
+      } else {
+        s = snap_c + sc0 + (int64_t)k * (2 * H);
+        as = (int64_t)(nr + 1) * (2 * H);
+      }
+      x.er = cer ? s[0] : R(0);
+      x.et = cet ? s[as] : R(0);
+      x.ep = cep ? s[2 * as] : R(0);
+      x.br = cbr ? s[3 * as] : R(0);
+      x.bt = cbt ? s[4 * as] : R(0);
+      x.bp = cbp ? s[5 * as] : R(0);
     }
-    const int b = (row < i_s) ? sy : sy + 1;                           // segment boundary
-    const int rr = row - (b * seg_rows - kFuseWarm);
-    return snap_r[(((int64_t)(b - 1) * kFuseArrays + a) * (kFuseWarm + kFuseTrail) + rr) * (nt + 1) + j];
+    x.b0r = cbr ? __ldg(f.br0 + kh) : R(0);
+    x.b0t = cbt ? __ldg(f.bt0 + kn) : R(0);
+    x.b0p = cbp ? __ldg(f.bp0 + kh) : R(0);
+    x.psi = cep ? __ldg(f.psi + kn) : P{};
+    x.tab = (k <= tlim) ? __ldg(tp + k) : R(0);
   };
-  const int k0 = max(0, i_s - kFuseWarm), k1 = min(nr, i_e) + 4;
+  auto fetch_src = [&](int k, FuseSrc<R> &y, auto tag) {
+    constexpr bool IN = decltype(tag)::value;
+    const bool node = IN || k <= nr, half = IN || k < nr;
+    const int64_t kn = (int64_t)k * n1 + j, kh = (int64_t)k * nt + j;
+    y.jr = (half && jn) ? __ldg(f.jr + kn) : R(0);
+    y.sr = (half && jn) ? __ldg(f.sr + kn) : R(0);
+    y.jt = (node && jh) ? __ldg(f.jt + kh) : R(0);
+    y.st = (node && jh) ? __ldg(f.st + kh) : R(0);
+    y.jp = (node && jn) ? __ldg(f.jp + kn) : R(0);
+    y.sp = (node && jn) ? __ldg(f.sp + kn) : R(0);
+  };
   // carve the rings
-  FuseRings<R> g;
+  FRing<R, kDEn> en_r, en_t, en_p;      // E^n            (half, node, node)
+  FRing<R, kDDbr> dbr;                  // dB_r^n         (node)
+  FRing<R, kDDbn> dbn_t, dbn_p;         // dB_th^n, dB_ph^n (half)
+  FRing<R, kDB0r> b0_r;                 // B_0,r          (node)
+  FRing<R, kDB0h> b0_t, b0_p;           // B_0,th, B_0,ph (half)
+  FRing<R, kDJp> jp_r, jp_t, jp_p;      // J_perp         (node)
+  FRing<R, kDBr> bh_r;                  // dB_r^{n+1/2}   (node)
+  FRing<R, kDBh> bh_t, bh_p;            // dB^{n+1/2}     (half)
+  FRing<R, kDE1r> e1_r;                 // E^{n+1} before the correction (half)
+  FRing<R, kDE1n> e1_t, e1_p;           //                                (node)
+  FRing<R, kDD> d_r, d_t, d_p;          // Delta E or E'' (node)
+  FRing<R, kDEc> ec_r, ec_t, ec_p;      // corrected E    (half, node, node)
+  FRing<P, kDPsi> psi;                  // Psi            (node)
+  R *tab;                               // radial tables, kDTab rows of kTabN
   {
     R *q = reinterpret_cast<R *>(fsmem);
     auto take = [&](int rows) { R *r = q; q += rows * NC; return r; };
-    g.en_r = take(kDEn); g.en_t = take(kDEn); g.en_p = take(kDEn);
-    g.dbn_t = take(kDEn); g.dbn_p = take(kDEn);
-    g.b0_r = take(kDB0n); g.b0_t = take(kDB0h); g.b0_p = take(kDB0h);
-    g.jp_r = take(kDJp); g.jp_t = take(kDJp); g.jp_p = take(kDJp);
-    g.bh_r = take(kDBh); g.bh_t = take(kDBh); g.bh_p = take(kDBh);
-    g.e1_r = take(kDEnr); g.e1_t = take(kDEnn); g.e1_p = take(kDEnn);
-    g.d_r = take(kDD); g.d_t = take(kDD); g.d_p = take(kDD);
-    g.ec_r = take(kDEc); g.ec_t = take(kDEc); g.ec_p = take(kDEc);
+    en_r.p = take(kDEn); en_t.p = take(kDEn); en_p.p = take(kDEn);
+    dbr.p = take(kDDbr); dbn_t.p = take(kDDbn); dbn_p.p = take(kDDbn);
+    b0_r.p = take(kDB0r); b0_t.p = take(kDB0h); b0_p.p = take(kDB0h);
+    jp_r.p = take(kDJp); jp_t.p = take(kDJp); jp_p.p = take(kDJp);
+    bh_r.p = take(kDBr); bh_t.p = take(kDBh); bh_p.p = take(kDBh);
+    e1_r.p = take(kDE1r); e1_t.p = take(kDE1n); e1_p.p = take(kDE1n);
+    d_r.p = take(kDD); d_t.p = take(kDD); d_p.p = take(kDD);
+    ec_r.p = take(kDEc); ec_t.p = take(kDEc); ec_p.p = take(kDEc);
+    tab = q;
+    q += kDTab * kTabN;
     uintptr_t a = reinterpret_cast<uintptr_t>(q);
     a = (a + 15) & ~uintptr_t(15);
-    g.psi = reinterpret_cast<P *>(a);
+    psi.p = reinterpret_cast<P *>(a);
   }
-  // ring accessors: (array, depth, row, column offset)
-  auto at = [&](R *ring, int depth, int row, int dc) -> R & { return ring[rs(row, depth) * NC + c + dc]; };
-  const Fields<R> &f = p.f;
-  const Tables<R> &t = p.t;
-  const R dt = p.dt, fp = R(4.0 * kPi) * p.dt;
+  auto T = [&](int row, int w) -> R { return tab[((unsigned)row % (unsigned)kDTab) * kTabN + w]; };
+  // theta tables of this column
+  const R sn0 = jn ? t.sn[j] : R(0), sn1 = jh ? t.sn[j + 1] : R(0), idcp = jh ? t.inv_dcp[j] : R(0);
+  const R sh0 = jh ? t.sh[j] : R(0), shm = (j >= 1 && j <= nt) ? t.sh[j - 1] : R(0);
+  const R idch = jn ? t.inv_dch[j] : R(0);
+  const R dt = p.dt, fp4 = R(4.0 * kPi) * p.dt;
   const bool lit = p.ff_interp_e != 0, filt = p.ff_sigma16 != R(0);
-  bool clamped_any = false;
+  const bool axis = (j == 0 || j == nt);
   unsigned long long nclamp = 0;
-  for (int k = k0; k <= k1; ++k) {
-    // ---------------------------------------------------------------- load
-    if (k <= nr) {
-      const int64_t kn = ix(k, j, n1), kh = ix(k, j, nt);
-      at(g.en_t, kDEn, k, 0) = jh ? src(1, f.et, nt, k) : R(0);
-      at(g.en_p, kDEn, k, 0) = jn ? src(2, f.ep, n1, k) : R(0);
-      at(g.b0_r, kDB0n, k, 0) = jh ? f.br0[kh] : R(0);
-      at(g.bh_r, kDBh, k, 0) = jh ? src(3, f.br, nt, k) : R(0);  // dB_r^n, advanced in place by F1 below
-      at(g.jp_r, kDJp, k, 0) = jn ? f.jpr[kn] : R(0);
-      at(g.jp_t, kDJp, k, 0) = jn ? f.jpt[kn] : R(0);
-      at(g.jp_p, kDJp, k, 0) = jn ? f.jpp[kn] : R(0);
-      g.psi[rs(k, kDPsi) * NC + c] = jn ? f.psi[kn] : P{};
-      if (k < nr) {
-        at(g.en_r, kDEn, k, 0) = jn ? src(0, f.er, n1, k) : R(0);
-        at(g.dbn_t, kDEn, k, 0) = jn ? src(4, f.bt, n1, k) : R(0);
-        at(g.dbn_p, kDEn, k, 0) = jh ? src(5, f.bp, nt, k) : R(0);
-        at(g.b0_t, kDB0h, k, 0) = jn ? f.bt0[kn] : R(0);
-        at(g.b0_p, kDB0h, k, 0) = jh ? f.bp0[kh] : R(0);
+  // blend weights of rows k-1, k-2, k-3 (E_r edge, E_th edge, node)
+  R fr1 = 0, fr2 = 0, fr3 = 0, ft1 = 0, ft2 = 0, ft3 = 0, fn1 = 0, fn2 = 0, fn3 = 0;
+  FuseRow<R> nx{};
+  FuseSrc<R> js{}, jsn{};
+  // F2: dB^{n+1} at node row k-4 and half row k-5 (own columns and rows)
+  auto f2 = [&](int k, auto tag) {
+    constexpr bool IN = decltype(tag)::value;
+    if (!own) return;
+    const int i = k - 4;  // B_r(i, j+1/2)
+    if ((IN || (i >= i_s && i < i_e)) && jh) {
+      const R cu = T(i, TB_INV_RN) * (sn1 * ec_p(i, c + 1) - sn0 * ec_p(i, c)) * idcp;
+      R v = bh_r(i, c) - hdt * cu;
+      const R sg = T(i, TB_SIG_N);
+      if (sg > R(0)) v -= sg * v;
+      f.br[(int64_t)i * nt + j] = v;
+    }
+    const int h = k - 5;  // B_th(h+1/2, j), B_ph(h+1/2, j+1/2)
+    if (IN || (h >= i_s && h < i_e && h < nr)) {
+      const R sg = T(h, TB_SIG_H), cb2 = T(h, TB_C_B2), rn0 = T(h, TB_RN), rn1 = T(h + 1, TB_RN);
+      if (jn) {
+        R v = R(0);
+        if (j > 0 && j < nt) {
+          v = bh_t(h, c) + hdt * cb2 * (rn1 * ec_p(h + 1, c) - rn0 * ec_p(h, c));
+          if (sg > R(0)) v -= sg * v;
+        }
+        f.bt[(int64_t)h * n1 + j] = v;
+      }
+      if (jh) {
+        const R cu = cb2 * (rn1 * ec_t(h + 1, c) - rn0 * ec_t(h, c)) - T(h, TB_C_BP2) * (ec_r(h, c + 1) - ec_r(h, c));
+        R w = bh_p(h, c) - hdt * cu;
+        if (sg > R(0)) w -= sg * w;
+        f.bp[(int64_t)h * nt + j] = w;
       }
     }
+  };
+  auto step = [&](int k, auto tag) {
+    constexpr bool IN = decltype(tag)::value;
+    // ------------------------------------------------------------ phase 0
+    f2(k, tag);
+    en_r(k, c) = nx.er; en_t(k, c) = nx.et; en_p(k, c) = nx.ep;
+    dbr(k, c) = nx.br; dbn_t(k, c) = nx.bt; dbn_p(k, c) = nx.bp;
+    b0_r(k, c) = nx.b0r; b0_t(k, c) = nx.b0t; b0_p(k, c) = nx.b0p;
+    psi(k, c) = nx.psi;
+    if (c < TB_COUNT) tab[((unsigned)k % (unsigned)kDTab) * kTabN + c] = nx.tab;
+    js = jsn;
+    fetch_src(k, jsn, tag);
+    if (IN || k + 1 <= kl) fetch(k + 1, nx, tag);
     __syncthreads();
-    // ------------------------------------------------------------------ F1
-    if (k <= nr && jh && c < NC - 1) {  // B_r(k, j+1/2)
-      const R cu = t.inv_rn[k] * (t.sn[j + 1] * at(g.en_p, kDEn, k, 1) - t.sn[j] * at(g.en_p, kDEn, k, 0)) *
-                   t.inv_dcp[j];
-      at(g.bh_r, kDBh, k, 0) -= hdt * cu;
+    // ------------------------------------------------------------ phase 1
+    if (IN || k <= nr) {
+      // B_r(k, j+1/2)
+      R v = dbr(k, c);
+      if (jh && c < NC - 1) v -= hdt * (T(k, TB_INV_RN) * (sn1 * en_p(k, c + 1) - sn0 * en_p(k, c)) * idcp);
+      bh_r(k, c) = v;
+      // J_perp(k, j) = rho E x B / B^2 from E^n, B^n
+      R jx = 0, jy = 0, jz = 0;
+      if ((IN || (k >= 1 && k < nr)) && jn && c >= 1) {
+        R e[3], b[3];
+        e[0] = R(0.5) * (en_r(k - 1, c) + en_r(k, c));
+        e[1] = axis ? R(0) : R(0.5) * (en_t(k, c - 1) + en_t(k, c));
+        e[2] = axis ? R(0) : en_p(k, c);
+        auto br = [&](int dc) { return b0_r(k, c + dc) + dbr(k, c + dc); };
+        auto bt = [&](int row) { return b0_t(row, c) + dbn_t(row, c); };
+        auto bp = [&](int row, int dc) { return b0_p(row, c + dc) + dbn_p(row, c + dc); };
+        b[0] = (j == 0) ? br(0) : (j == nt) ? br(-1) : R(0.5) * (br(-1) + br(0));
+        b[1] = axis ? R(0) : R(0.5) * (bt(k - 1) + bt(k));
+        b[2] = axis ? R(0) : R(0.25) * (bp(k - 1, -1) + bp(k - 1, 0) + bp(k, -1) + bp(k, 0));
+        const R div = T(k, TB_RHO_A) * (T(k, TB_RH2) * en_r(k, c) - T(k - 1, TB_RH2) * en_r(k - 1, c));
+        R dth = 0;
+        if (j < nt) dth += sh0 * en_t(k, c);
+        if (j > 0) dth -= shm * en_t(k, c - 1);
+        const R rho = div + T(k, TB_RHO_B) * dth * idch;
+        const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        if (b2 > b2min<R>()) {
+          const R s = rho / b2;
+          jx = s * (e[1] * b[2] - e[2] * b[1]);
+          jy = s * (e[2] * b[0] - e[0] * b[2]);
+          jz = s * (e[0] * b[1] - e[1] * b[0]);
+        }
+      }
+      jp_r(k, c) = jx; jp_t(k, c) = jy; jp_p(k, c) = jz;
+      if (own && jn && (IN || (k >= i_s && k < i_e))) {
+        const int64_t kk = (int64_t)k * n1 + j;
+        f.jpr[kk] = jx; f.jpt[kk] = jy; f.jpp[kk] = jz;
+      }
     }
-    if (k >= 1 && k - 1 < nr) {
+    if (IN || (k >= 1 && k - 1 < nr)) {
       const int i = k - 1;
+      const R cb2 = T(i, TB_C_B2), rn0 = T(i, TB_RN), rn1 = T(k, TB_RN);
       R v = R(0);  // B_th(i+1/2, j): zero on the axis
-      if (j > 0 && j < nt)
-        v = at(g.dbn_t, kDEn, i, 0) +
-            hdt * t.c_b2[i] * (t.rn[i + 1] * at(g.en_p, kDEn, i + 1, 0) - t.rn[i] * at(g.en_p, kDEn, i, 0));
-      at(g.bh_t, kDBh, i, 0) = v;
+      if (j > 0 && j < nt) v = dbn_t(i, c) + hdt * cb2 * (rn1 * en_p(k, c) - rn0 * en_p(i, c));
+      bh_t(i, c) = v;
       if (jh && c < NC - 1) {  // B_ph(i+1/2, j+1/2)
-        const R cu = t.c_b2[i] * (t.rn[i + 1] * at(g.en_t, kDEn, i + 1, 0) - t.rn[i] * at(g.en_t, kDEn, i, 0)) -
-                     t.c_bp2[i] * (at(g.en_r, kDEn, i, 1) - at(g.en_r, kDEn, i, 0));
-        at(g.bh_p, kDBh, i, 0) = at(g.dbn_p, kDEn, i, 0) - hdt * cu;
+        const R cu = cb2 * (rn1 * en_t(k, c) - rn0 * en_t(i, c)) - T(i, TB_C_BP2) * (en_r(i, c + 1) - en_r(i, c));
+        bh_p(i, c) = dbn_p(i, c) - hdt * cu;
       }
     }
     __syncthreads();
-    // ------------------------------------------------------------------- A
-    if (k >= 1 && k - 1 <= nr && c >= 1 && c < NC - 1) {
+    // ------------------------------------------------------------ phase 2
+    fr3 = fr2; fr2 = fr1; ft3 = ft2; ft2 = ft1; fn3 = fn2; fn2 = fn1;
+    fr1 = 0; ft1 = 0; fn1 = 0;
+    if ((IN || (k >= 1 && k - 1 <= nr)) && c >= 1 && c < NC - 1) {  // A at row i = k-1
       const int i = k - 1;
-      auto psi_at = [&](int row, int dc) { return g.psi[rs(row, kDPsi) * NC + c + dc]; };
-      if (i < nr && jn) {  // E_r(i+1/2, j)
+      if ((IN || i < nr) && jn) {  // E_r(i+1/2, j)
         R cu = R(0);
-        if (j < nt) cu += t.sh[j] * at(g.bh_p, kDBh, i, 0);
-        if (j > 0) cu -= t.sh[j - 1] * at(g.bh_p, kDBh, i, -1);
-        cu *= t.inv_rh[i] * t.inv_dch[j];
-        const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i + 1, 0)));
-        const bool lo = i >= 1, hi = i + 1 <= nr - 1;
+        if (j < nt) cu += sh0 * bh_p(i, c);
+        if (j > 0) cu -= shm * bh_p(i, c - 1);
+        cu *= T(i, TB_INV_RH) * idch;
+        const R fb = blend(p, psi_mean2(psi(i, c), psi(i + 1, c)));
+        fr1 = fb;
+        const bool lo = IN || i >= 1, hi = IN || i + 1 <= nr - 1;
         R jm = R(0);
-        if (lo) jm += at(g.jp_r, kDJp, i, 0);
-        if (hi) jm += at(g.jp_r, kDJp, i + 1, 0);
+        if (lo) jm += jp_r(i, c);
+        if (hi) jm += jp_r(i + 1, c);
         if (lo && hi) jm *= R(0.5);
-        const int64_t kk = ix(i, j, n1);
-        const R jt = (R(1) - fb) * f.jr[kk] + fb * jm;
-        at(g.e1_r, kDEnr, i, 0) = (at(g.en_r, kDEn, i, 0) + dt * (cu + f.sr[kk]) - fp * jt) * (R(1) - t.sig_h[i]);
+        const R jt = (R(1) - fb) * js.jr + fb * jm;
+        e1_r(i, c) = (en_r(i, c) + dt * (cu + js.sr) - fp4 * jt) * (R(1) - T(i, TB_SIG_H));
       }
       if (jh) {  // E_th(i, j+1/2)
-        const int64_t kk = ix(i, j, nt);
         R v;
-        if (i == 0) {
-          v = -p.omega * t.rn[0] * t.sh[j] * (at(g.b0_r, kDB0n, 0, 0) + at(g.bh_r, kDBh, 0, 0));
-        } else if (i == nr) {
+        if (!IN && i == 0) {
+          v = -p.omega * T(0, TB_RN) * sh0 * (b0_r(0, c) + bh_r(0, c));
+        } else if (!IN && i == nr) {
           v = R(0);
         } else {
-          const R cu = -t.c_e2[i] * (t.rh[i] * at(g.bh_p, kDBh, i, 0) - t.rh[i - 1] * at(g.bh_p, kDBh, i - 1, 0));
-          const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i, 1)));
-          const R jt = (R(1) - fb) * f.jt[kk] + fb * R(0.5) * (at(g.jp_t, kDJp, i, 0) + at(g.jp_t, kDJp, i, 1));
-          v = (at(g.en_t, kDEn, i, 0) + dt * (cu + f.st[kk]) - fp * jt) * (R(1) - t.sig_n[i]);
+          const R cu = -T(i, TB_C_E2) * (T(i, TB_RH) * bh_p(i, c) - T(i - 1, TB_RH) * bh_p(i - 1, c));
+          const R fb = blend(p, psi_mean2(psi(i, c), psi(i, c + 1)));
+          ft1 = fb;
+          const R jt = (R(1) - fb) * js.jt + fb * R(0.5) * (jp_t(i, c) + jp_t(i, c + 1));
+          v = (en_t(i, c) + dt * (cu + js.st) - fp4 * jt) * (R(1) - T(i, TB_SIG_N));
         }
-        at(g.e1_t, kDEnn, i, 0) = v;
+        e1_t(i, c) = v;
       }
       if (jn) {  // E_ph(i, j)
-        const int64_t kk = ix(i, j, n1);
         R v = R(0);
-        if (i >= 1 && i < nr && j >= 1 && j < nt) {
-          const R cu = t.c_e2[i] * (t.rh[i] * at(g.bh_t, kDBh, i, 0) - t.rh[i - 1] * at(g.bh_t, kDBh, i - 1, 0)) -
-                       t.c_ep2[i] * (at(g.bh_r, kDBh, i, 0) - at(g.bh_r, kDBh, i, -1));
-          const R fb = blend(p, psi_at(i, 0));
-          const R jt = (R(1) - fb) * f.jp[kk] + fb * at(g.jp_p, kDJp, i, 0);
-          v = (at(g.en_p, kDEn, i, 0) + dt * (cu + f.sp[kk]) - fp * jt) * (R(1) - t.sig_n[i]);
+        if ((IN || (i >= 1 && i < nr)) && j >= 1 && j < nt) {
+          const R cu = T(i, TB_C_E2) * (T(i, TB_RH) * bh_t(i, c) - T(i - 1, TB_RH) * bh_t(i - 1, c)) -
+                       T(i, TB_C_EP2) * (bh_r(i, c) - bh_r(i, c - 1));
+          const R fb = blend(p, psi(i, c));
+          fn1 = fb;
+          const R jt = (R(1) - fb) * js.jp + fb * jp_p(i, c);
+          v = (en_p(i, c) + dt * (cu + js.sp) - fp4 * jt) * (R(1) - T(i, TB_SIG_N));
         }
-        at(g.e1_p, kDEnn, i, 0) = v;
+        e1_p(i, c) = v;
       }
     }
-    __syncthreads();
-    // ------------------------------------------------------------------- N
-    if (k >= 1 && k - 1 <= nr && c >= 1 && c < NC - 1) {
-      const int i = k - 1;
+    if ((IN || (k >= 2 && k - 2 <= nr)) && c >= 1) {  // N at node row i = k-2
+      const int i = k - 2;
+      const bool orow = IN || (i >= i_s && i < i_e);
       R d0 = 0, d1 = 0, d2 = 0;
-      if (i >= 1 && i < nr && jn) {
-        const bool axis = (j == 0 || j == nt);
+      if ((IN || (i >= 1 && i < nr)) && jn) {
         R e[3], b[3];
-        e[0] = R(0.5) * (at(g.e1_r, kDEnr, i - 1, 0) + at(g.e1_r, kDEnr, i, 0));
-        e[1] = axis ? R(0) : R(0.5) * (at(g.e1_t, kDEnn, i, -1) + at(g.e1_t, kDEnn, i, 0));
-        e[2] = axis ? R(0) : at(g.e1_p, kDEnn, i, 0);
-        auto br = [&](int dc) { return at(g.b0_r, kDB0n, i, dc) + at(g.bh_r, kDBh, i, dc); };
-        auto bt = [&](int row) { return at(g.b0_t, kDB0h, row, 0) + at(g.bh_t, kDBh, row, 0); };
-        auto bp = [&](int row, int dc) { return at(g.b0_p, kDB0h, row, dc) + at(g.bh_p, kDBh, row, dc); };
+        e[0] = R(0.5) * (e1_r(i - 1, c) + e1_r(i, c));
+        e[1] = axis ? R(0) : R(0.5) * (e1_t(i, c - 1) + e1_t(i, c));
+        e[2] = axis ? R(0) : e1_p(i, c);
+        auto br = [&](int dc) { return b0_r(i, c + dc) + bh_r(i, c + dc); };
+        auto bt = [&](int row) { return b0_t(row, c) + bh_t(row, c); };
+        auto bp = [&](int row, int dc) { return b0_p(row, c + dc) + bh_p(row, c + dc); };
         b[0] = (j == 0) ? br(0) : (j == nt) ? br(-1) : R(0.5) * (br(-1) + br(0));
         b[1] = axis ? R(0) : R(0.5) * (bt(i - 1) + bt(i));
         b[2] = axis ? R(0) : R(0.25) * (bp(i - 1, -1) + bp(i - 1, 0) + bp(i, -1) + bp(i, 0));
@@ -690,122 +856,101 @@ __global__ void __launch_bounds__(kFuseThreads) k_field_fused(Params<R> p, R hdt
           d0 = sc * x - e[0];
           d1 = sc * y - e[1];
           d2 = sc * z - e[2];
-          if (e2 > b2 && own && i >= i_s && i < i_e) { clamped_any = true; ++nclamp; }
+          if (e2 > b2 && own && orow) ++nclamp;
         }
         if (lit) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
       }
-      at(g.d_r, kDD, i, 0) = d0;
-      at(g.d_t, kDD, i, 0) = d1;
-      at(g.d_p, kDD, i, 0) = d2;
-      if (own && jn && i >= i_s && i < i_e) {
-        const int64_t kk = ix(i, j, n1);
+      d_r(i, c) = d0; d_t(i, c) = d1; d_p(i, c) = d2;
+      if (own && jn && orow) {
+        const int64_t kk = (int64_t)i * n1 + j;
         f.der[kk] = d0; f.det[kk] = d1; f.dep[kk] = d2;
       }
     }
     __syncthreads();
-    // ------------------------------------------------------------------- C
-    if (k >= 3 && k - 3 <= nr && c >= 2 && c < NC - 2) {
+    // ------------------------------------------------------------ phase 3
+    if ((IN || (k >= 3 && k - 3 <= nr)) && c >= 2 && c < NC - 2) {  // C at row i = k-3
       const int i = k - 3;
-      auto psi_at = [&](int row, int dc) { return g.psi[rs(row, kDPsi) * NC + c + dc]; };
-      if (i < nr && jn) {  // E_r(i+1/2, j)
-        R v = at(g.e1_r, kDEnr, i, 0);
-        const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i + 1, 0)));
+      const bool out = own && (IN || (i >= i_s && i < i_e));
+      if ((IN || i < nr) && jn) {  // E_r(i+1/2, j)
+        R v = e1_r(i, c);
+        const R fb = fr3;
         if (fb != R(0)) {
-          const bool lo = i >= 1, hi = i + 1 <= nr - 1;
+          const bool lo = IN || i >= 1, hi = IN || i + 1 <= nr - 1;
           R m = R(0);
-          if (lo) m += at(g.d_r, kDD, i, 0);
-          if (hi) m += at(g.d_r, kDD, i + 1, 0);
+          if (lo) m += d_r(i, c);
+          if (hi) m += d_r(i + 1, c);
           if (lo && hi) m *= R(0.5);
-          if (filt && i >= 2 && i <= nr - 3)
-            m -= p.ff_sigma16 * (at(g.e1_r, kDEnr, i - 2, 0) - R(4) * at(g.e1_r, kDEnr, i - 1, 0) + R(6) * v -
-                                 R(4) * at(g.e1_r, kDEnr, i + 1, 0) + at(g.e1_r, kDEnr, i + 2, 0));
+          if (filt && (IN || (i >= 2 && i <= nr - 3)))
+            m -= p.ff_sigma16 * (e1_r(i - 2, c) - R(4) * e1_r(i - 1, c) + R(6) * v - R(4) * e1_r(i + 1, c) +
+                                 e1_r(i + 2, c));
           v += fb * (lit ? m - v : m);
         }
-        at(g.ec_r, kDEc, i, 0) = v;
-        if (own && i >= i_s && i < i_e) f.er[ix(i, j, n1)] = v;
+        ec_r(i, c) = v;
+        if (out) f.er[(int64_t)i * n1 + j] = v;
       }
       if (jh) {  // E_th(i, j+1/2)
-        R v = at(g.e1_t, kDEnn, i, 0);
-        if (i >= 1 && i < nr) {
-          const R fb = blend(p, psi_mean2(psi_at(i, 0), psi_at(i, 1)));
+        R v = e1_t(i, c);
+        if (IN || (i >= 1 && i < nr)) {
+          const R fb = ft3;
           if (fb != R(0)) {
-            R m = R(0.5) * (at(g.d_t, kDD, i, 0) + at(g.d_t, kDD, i, 1));
+            R m = R(0.5) * (d_t(i, c) + d_t(i, c + 1));
             if (filt && j >= 2 && j <= nt - 3)
-              m -= p.ff_sigma16 * (at(g.e1_t, kDEnn, i, -2) - R(4) * at(g.e1_t, kDEnn, i, -1) + R(6) * v -
-                                   R(4) * at(g.e1_t, kDEnn, i, 1) + at(g.e1_t, kDEnn, i, 2));
+              m -= p.ff_sigma16 * (e1_t(i, c - 2) - R(4) * e1_t(i, c - 1) + R(6) * v - R(4) * e1_t(i, c + 1) +
+                                   e1_t(i, c + 2));
             v += fb * (lit ? m - v : m);
           }
         }
-        at(g.ec_t, kDEc, i, 0) = v;
-        if (own && i >= i_s && i < i_e) f.et[ix(i, j, nt)] = v;
+        ec_t(i, c) = v;
+        if (out) f.et[(int64_t)i * nt + j] = v;
       }
       if (jn) {  // E_ph(i, j)
-        R v = at(g.e1_p, kDEnn, i, 0);
-        if (i >= 1 && i < nr && j >= 1 && j < nt) {
-          const R fb = blend(p, psi_at(i, 0));
+        R v = e1_p(i, c);
+        if ((IN || (i >= 1 && i < nr)) && j >= 1 && j < nt) {
+          const R fb = fn3;
           if (fb != R(0)) {
-            const R m = at(g.d_p, kDD, i, 0);
+            const R m = d_p(i, c);
             v += fb * (lit ? m - v : m);
           }
         }
-        at(g.ec_p, kDEc, i, 0) = v;
-        if (own && i >= i_s && i < i_e) f.ep[ix(i, j, n1)] = v;
+        ec_p(i, c) = v;
+        if (out) f.ep[(int64_t)i * n1 + j] = v;
       }
     }
     __syncthreads();
-    // ------------------------------------------------------------------ F2
-    if (own) {
-      if (k >= 3 && k - 3 <= nr && jh) {  // B_r(i, j+1/2), i = k-3
-        const int i = k - 3;
-        const R cu = t.inv_rn[i] * (t.sn[j + 1] * at(g.ec_p, kDEc, i, 1) - t.sn[j] * at(g.ec_p, kDEc, i, 0)) *
-                     t.inv_dcp[j];
-        R v = at(g.bh_r, kDBh, i, 0) - hdt * cu;
-        const R sg = t.sig_n[i];
-        if (sg > R(0)) v -= sg * v;
-        if (i >= i_s && i < i_e) f.br[ix(i, j, nt)] = v;
-      }
-      if (k >= 4 && k - 4 < nr) {  // B_th, B_ph at half row i = k-4
-        const int i = k - 4;
-        if (i >= i_s && i < i_e) {
-          if (jn) {
-            R v = R(0);
-            if (j > 0 && j < nt) {
-              v = at(g.bh_t, kDBh, i, 0) +
-                  hdt * t.c_b2[i] * (t.rn[i + 1] * at(g.ec_p, kDEc, i + 1, 0) - t.rn[i] * at(g.ec_p, kDEc, i, 0));
-              const R sg = t.sig_h[i];
-              if (sg > R(0)) v -= sg * v;
-            }
-            f.bt[ix(i, j, n1)] = v;
-          }
-          if (jh) {
-            const R cu = t.c_b2[i] * (t.rn[i + 1] * at(g.ec_t, kDEc, i + 1, 0) - t.rn[i] * at(g.ec_t, kDEc, i, 0)) -
-                         t.c_bp2[i] * (at(g.ec_r, kDEc, i, 1) - at(g.ec_r, kDEc, i, 0));
-            R w = at(g.bh_p, kDBh, i, 0) - hdt * cu;
-            const R sg = t.sig_h[i];
-            if (sg > R(0)) w -= sg * w;
-            f.bp[ix(i, j, nt)] = w;
-          }
-        }
-      }
-    }
-    __syncthreads();  // the next step's loads reuse ring slots
+  };
+  // interior steps: rows k-5 .. k+1 own (k-5 >= i_s, k+1 < i_e) and inside
+  // rows 2 .. nr-3 (k >= 7, k+4 <= nr)
+  const int kin0 = max(i_s + 5, 7), kin1 = min(i_e - 2, nr - 4);
+  fetch(k0, nx, std::false_type{});
+  for (int k = k0; k <= kl; ++k) {
+    if (k >= kin0 && k <= kin1) step(k, std::true_type{});
+    else step(k, std::false_type{});
   }
+  f2(kl + 1, std::false_type{});
   // running count of Eq. 26 activations (see k_node_b)
-  const unsigned m = __ballot_sync(0xffffffffu, clamped_any);
   unsigned long long tot = nclamp;
   for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-  if (m && (threadIdx.x & 31) == 0 && tot) atomicAdd(p.clamps, tot);
+  if ((threadIdx.x & 31) == 0 && tot) atomicAdd(p.clamps, tot);
 }
 
 template <typename R> size_t field_fused_smem() { return fuse_smem_bytes<R>(); }
 template <typename R> const void *field_fused_fn() { return reinterpret_cast<const void *>(&k_field_fused<R>); }
 template <typename R> cudaError_t set_field_fused_smem(size_t bytes) { return raise_smem_limit<field_fused_fn<R>>(bytes); }
-// rows per segment: enough blocks for the GPU (about eight per SM), at
-// least 32 rows so that the warm-up stays a small share
-int fuse_seg_rows(int nr, int nt, int n_sm) {
+// rows per segment: as many segments as fit the strips into wave_blocks
+// resident blocks (one wave: every block walks its rows once, none waits
+// for a second wave), at least 32 rows so that the warm-up stays a small
+// share
+int fuse_seg_rows(int nr, int nt, int wave_blocks) {
   const int strips = (nt + 1 + kFuseOwn - 1) / kFuseOwn;
-  const int want = std::max(1, (8 * n_sm + strips - 1) / strips);
-  return std::max(32, (nr + 1 + want - 1) / want);
+  const int segs = std::max(1, wave_blocks / strips);
+  return std::max(32, (nr + 1 + segs - 1) / segs);
+}
+template <typename R> int field_fused_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_field_fused<R>, kFuseThreads, fuse_smem_bytes<R>()) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real) {
   const FuseGeom fg = fuse_geom(nr, nt, seg_rows);
@@ -815,9 +960,35 @@ template <typename R> void launch_field_fused(const Params<R> &p, int seg_rows, 
   const FuseGeom fg = fuse_geom(p.nr, p.nt, seg_rows);
   R *sc = reinterpret_cast<R *>(snap);
   R *sr = sc + fuse_snap_cols(p.nr, fg.strips);
-  const int64_t n = fuse_snap_cols(p.nr, fg.strips) + fuse_snap_rows(p.nt, fg.segs);
-  if (n > 0) k_fuse_snap<R><<<(unsigned)std::min<int64_t>((n + 255) / 256, 16384), 256, 0, s>>>(p, sc, sr, fg);
+  if (fg.strips > 1)
+    k_fuse_snap_cols<R><<<dim3((p.nr + 1 + 31) / 32, (fg.strips - 1) * kFuseArrays), dim3(2 * kFuseHalo, 32), 0, s>>>(
+        p, sc);
+  if (fg.segs > 1)
+    k_fuse_snap_rows<R><<<dim3((p.nt + 1 + 255) / 256, kFuseWarm + kFuseTrail, (fg.segs - 1) * kFuseArrays), 256, 0,
+                          s>>>(p, sr, seg_rows);
   k_field_fused<R><<<dim3(fg.strips, fg.segs), kFuseThreads, fuse_smem_bytes<R>(), s>>>(p, R(0.5) * p.dt, fg, sc, sr);
+}
+
+// The per-cell pure force-free flag f(Psi_cell) >= 1 (used to remove
+// particles, Eq. 29) on its own, for the fused field update, which computes
+// J_perp itself: a thread walks kFfRows cells of one column, reading every
+// node row of Psi once (the arithmetic of ff_cell).
+constexpr int kFfRows = 16;
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads) k_ffcell(Params<R> p) {
+  using P = typename PsiOf<R>::T;
+  const int nr = p.nr, nt = p.nt, n1 = nt + 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i0 = blockIdx.y * kFfRows;
+  if (j >= nt || i0 >= nr) return;
+  const int i1 = min(i0 + kFfRows, nr);
+  const P *psi = p.f.psi + j;
+  P a = psi[(int64_t)i0 * n1], b = psi[(int64_t)i0 * n1 + 1];
+  for (int i = i0; i < i1; ++i) {
+    const P c = psi[(int64_t)(i + 1) * n1], d = psi[(int64_t)(i + 1) * n1 + 1];
+    p.f.ffcell[(int64_t)i * nt + j] = blend(p, psi_mean4(a, c, b, d)) >= R(1) ? 1 : 0;
+    a = c;
+    b = d;
+  }
 }
 
 // The blend weights of the last flux prefix, on request (hff_fields): f at
@@ -845,6 +1016,9 @@ template <typename R> const void *psi_fn() { return reinterpret_cast<const void 
 template <typename R> cudaError_t set_psi_smem(size_t bytes) { return raise_smem_limit<psi_fn<R>>(bytes); }
 template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s) {
   k_node_a<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p);
+}
+template <typename R> void launch_ffcell(const Params<R> &p, cudaStream_t s) {
+  k_ffcell<R><<<dim3((p.nt + kRowThreads - 1) / kRowThreads, (p.nr + kFfRows - 1) / kFfRows), kRowThreads, 0, s>>>(p);
 }
 template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s) {
   k_faraday<R><<<row_grid(p.nr + 1, p.nt), kRowThreads, 0, s>>>(p, half * p.dt, absorb);
@@ -878,13 +1052,15 @@ template <typename R> void launch_combine(R *dst, const R *a, const R *b, int64_
   template cudaError_t set_psi_smem<R>(size_t);                                \
   template size_t psi_smem<R>(int);                                            \
   template void launch_node_a<R>(const Params<R> &, cudaStream_t);             \
+  template void launch_ffcell<R>(const Params<R> &, cudaStream_t);             \
   template void launch_faraday<R>(const Params<R> &, R, bool, cudaStream_t);   \
   template void launch_ampere<R>(const Params<R> &, cudaStream_t);             \
   template void launch_correct<R>(const Params<R> &, cudaStream_t);            \
   template void launch_blend_out<R>(const Params<R> &, R *, R *, R *, uint8_t *, cudaStream_t); \
   template void launch_field_fused<R>(const Params<R> &, int, void *, cudaStream_t);            \
   template size_t field_fused_smem<R>();                                                         \
-  template cudaError_t set_field_fused_smem<R>(size_t);
+  template cudaError_t set_field_fused_smem<R>(size_t);                                          \
+  template int field_fused_blocks_per_sm<R>();
 HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST

@@ -237,6 +237,8 @@ template <typename R> void launch_psi(const Params<R> &p, cudaStream_t s);
 template <typename R> cudaError_t set_psi_smem(size_t bytes);
 template <typename R> size_t psi_smem(int nt);  // dynamic shared memory of the flux prefix
 template <typename R> void launch_node_a(const Params<R> &p, cudaStream_t s);
+// the per-cell force-free flags alone (the fused field update computes J_perp)
+template <typename R> void launch_ffcell(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_faraday(const Params<R> &p, R half, bool absorb, cudaStream_t s);
 template <typename R> void launch_ampere(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_correct(const Params<R> &p, cudaStream_t s);
@@ -247,7 +249,8 @@ template <typename R> void launch_blend_out(const Params<R> &p, R *fr, R *ft, R 
 // Ampere, renormalisation, return, Faraday half with absorber) in one pass
 // over row segments of seg_rows rows
 template <typename R> void launch_field_fused(const Params<R> &p, int seg_rows, void *snap, cudaStream_t s);
-int fuse_seg_rows(int nr, int nt, int n_sm);                        // rows per segment of the launch
+int fuse_seg_rows(int nr, int nt, int wave_blocks);                 // rows per segment of the launch
+template <typename R> int field_fused_blocks_per_sm();              // its occupancy (0 = unknown)
 size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real);  // its halo snapshot
 template <typename R> size_t field_fused_smem();
 template <typename R> cudaError_t set_field_fused_smem(size_t bytes);

@@ -30,6 +30,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhff.so")
 HFF_OK, HFF_ERR_ARG, HFF_ERR_CAPACITY, HFF_ERR_CUDA, HFF_ERR_TIMEOUT, HFF_ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 GEOM = {"dipole": 0, "monopole": 1, "synth": 2, "uniform": 3, "michel": 4}
 FP32, FP64 = 0, 1
+# hff_config.field_pass: the field update as one fused pass, or split in
+# four kernels
+FIELDS_FUSED, FIELDS_SPLIT = 0, 1
+FIELD_PASS_DEFAULT = FIELDS_FUSED
 HOST, DEVICE = 0, 1
 ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255, nocount=256)
 SCALAR_RR_SCALE = 0
@@ -58,7 +62,7 @@ class hff_config(C.Structure):
         ("capacity", C.c_int64), ("tile_r", C.c_int32), ("tile_t", C.c_int32),
         ("sort_every", C.c_int32), ("precision", C.c_int32),
         ("gamma_th", C.c_double), ("gamma_s", C.c_double), ("inject_species", C.c_int32 * 2),
-        ("ff_delta_only", C.c_int32), ("ff_filter", C.c_double),
+        ("ff_delta_only", C.c_int32), ("ff_filter", C.c_double), ("field_pass", C.c_int32),
     ]
 
 
@@ -183,6 +187,7 @@ def config_struct(cfg: dict) -> hff_config:
     c.inject_species[0], c.inject_species[1] = int(isp[0]), int(isp[1])
     c.ff_delta_only = int(cfg.get("ff_delta_only", 0))
     c.ff_filter = float(cfg.get("ff_filter", 0.0))
+    c.field_pass = int(cfg.get("field_pass", FIELD_PASS_DEFAULT))
     return c
 
 

@@ -47,7 +47,8 @@ def test_plan_sizes_scale_with_grid_and_capacity(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=33), dict(n_breaks_bad=True),
-                                 dict(r_abs="one_cell_inside"), dict(precision_bad=True)])
+                                 dict(r_abs="one_cell_inside"), dict(precision_bad=True),
+                                 dict(field_pass_bad=True)])
 def test_invalid_configs_are_rejected(lib, bad):
     cfg = workloads.config("small_pic")
     cfg.update(capacity=10)
@@ -65,6 +66,8 @@ def test_invalid_configs_are_rejected(lib, bad):
         c.r_abs = c.r_max * (c.r_max / c.r_min) ** (-1.0 / c.nr)
     if "precision_bad" in bad:
         c.precision = 7
+    if "field_pass_bad" in bad:
+        c.field_pass = 2
     with pytest.raises(hff.HffError) as e:
         hff.hff_plan(c)
     assert e.value.code == hff.HFF_ERR_ARG
