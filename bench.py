@@ -336,6 +336,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--tile", default=None, help="tile_r x tile_t of the sort and the tiled push, e.g. 16x24")
     ap.add_argument("--sort-every", type=int, default=None)
+    ap.add_argument("--order", default="scattered", choices=["scattered", "cell"],
+                    help="particle order at load: as generated (scattered within each tile) or sorted by cell, "
+                         "the order co-located injected pairs take in a long run")
     ap.add_argument("--field-pass", type=int, default=None, choices=[0, 1],
                     help="field update: 0 = one fused pass (the default), 1 = four kernels")
     ap.add_argument("--oracle-sample", default="128", choices=["128", "full"],
@@ -385,6 +388,10 @@ def main():
     prec = cfg.get("precision", "fp32")
     t0 = time.perf_counter()
     ps = workloads.particles(cfg, threads=16)
+    if args.order == "cell":
+        for sp in range(len(ps)):
+            order = np.argsort(ps[sp]["cell"], kind="stable")
+            ps[sp] = {k: v[order] for k, v in ps[sp].items()}
     keep_fp64 = prec == "fp32" and ws == 1 and not args.no_fp64_compare
     ps_keep = ps if keep_fp64 else None
     log(f"[bench] rank {rank}: generated {2 * cfg['n_pairs']} particles in {time.perf_counter() - t0:.1f} s")
@@ -556,6 +563,7 @@ def main():
             "sort_every": cfg["sort_every"],
             "tile": [cfg["tile_r"], cfg["tile_t"]],
             "field_pass": int(cfg.get("field_pass", hff.FIELD_PASS_DEFAULT)),
+            "particle_order": args.order,
             "launch_shape": tuned or "configured",
             "l2": "inputs larger than L2 (particle state %.1f GB)" % (n_live0 * (28 if prec == "fp32" else 52) / 1e9),
             "parallelism": "replicas" if ws > 1 else "single",

@@ -342,9 +342,86 @@ __device__ __forceinline__ Axis<R> axis_weights(R x0, R X1) {
   return w;
 }
 
+// With `runs` (a work item whose particles sit cell by cell, decided once
+// per item), lanes of a warp that deposit into the same windows (equal J_r
+// / J_th window base and equal J_ph base) and sit next to each other form a
+// run; with at least kRunMin such neighbours in the warp, a segmented scan
+// sums each run's 16 site values and only the run's last lane issues the
+// shared atomics.  FP32 (and FP64) shared atomic adds are compare-and-swap
+// loops on this GPU, which serialise on equal addresses: particles of one
+// cell next to each other in memory (co-located injected pairs, or any
+// cell-coherent order) otherwise cost one retry per lane and site (a
+// cell-ordered 4096^2 workload measured 2.7x the push time of a scattered
+// order).
+constexpr int kRunMin = 4;
+constexpr int kRunItemMin = 16;  // equal neighbour cells among 256 sampled pairs of a work item
+template <typename R>
+__device__ __forceinline__ void deposit_sh_runs(const SharedMesh<R> &m, R qw, int i0, int j0, R x0, R y0, R X1,
+                                                R Y1, R vphi) {
+  const Axis<R> ax = axis_weights(x0, X1), ay = axis_weights(y0, Y1);
+  const R nq = -qw;
+  const int lt = m.lt;
+  const int ob = m.o(i0 - 1 + ax.a0, j0 - 1 + ay.a0);
+  R v[16];
+  {
+    const R g0 = nq * ax.f0, g1 = nq * ax.f1;
+    v[0] = g0 * ay.m0; v[1] = g0 * ay.m1; v[2] = g0 * ay.m2;
+    v[3] = g1 * ay.m0; v[4] = g1 * ay.m1; v[5] = g1 * ay.m2;
+  }
+  {
+    const R g0 = nq * ay.f0, g1 = nq * ay.f1;
+    v[6] = g0 * ax.m0; v[7] = g0 * ax.m1; v[8] = g0 * ax.m2;
+    v[9] = g1 * ax.m0; v[10] = g1 * ax.m1; v[11] = g1 * ax.m2;
+  }
+  int op;
+  {
+    const R xm = R(0.5) * (x0 + X1), ym = R(0.5) * (y0 + Y1);
+    const int km = (xm < R(0)) ? -1 : (xm < R(1) ? 0 : 1);
+    const int lm = (ym < R(0)) ? -1 : (ym < R(1) ? 0 : 1);
+    const R wx = xm - R(km), wy = ym - R(lm);
+    const R qv = qw * vphi;
+    const R a0 = qv * (R(1) - wx), a1 = qv * wx;
+    v[12] = a0 * (R(1) - wy); v[13] = a0 * wy; v[14] = a1 * (R(1) - wy); v[15] = a1 * wy;
+    op = m.o(i0 + km, j0 + lm);
+  }
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int pob = __shfl_up_sync(act, ob, 1), pop = __shfl_up_sync(act, op, 1);
+  const bool cont = lane > 0 && ((act >> (lane - 1)) & 1u) && pob == ob && pop == op;
+  const unsigned conts = __ballot_sync(act, cont);
+  if (__popc(conts) >= kRunMin) {  // the same decision in every lane of act
+    // a run starts at every lane that does not continue its predecessor
+    // (inactive lanes included), so a run holds active lanes only
+    const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+    const int start = 31 - __clz(~conts & upto);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const R y = __shfl_up_sync(act, v[k], d);
+        if (lane - d >= start) v[k] += y;
+      }
+    }
+    if (lane < 31 && ((conts >> (lane + 1)) & 1u)) return;  // not the run's last lane
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    if (v[k] != R(0)) atomicAdd(&m.s_jr[ob + (k / 3) * lt + k % 3], v[k]);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    if (v[6 + k] != R(0)) atomicAdd(&m.s_jt[ob + (k % 3) * lt + k / 3], v[6 + k]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (v[12 + k] != R(0)) atomicAdd(&m.s_jp[op + (k / 2) * lt + k % 2], v[12 + k]);
+}
+
 template <typename R>
 __device__ __forceinline__ void deposit_sh(const SharedMesh<R> &m, R qw, int i0, int j0, R x0, R y0, R X1, R Y1,
-                                           R vphi) {
+                                           R vphi, bool runs) {
+  if (runs) {
+    deposit_sh_runs<R>(m, qw, i0, j0, x0, y0, X1, Y1, vphi);
+    return;
+  }
   const Axis<R> ax = axis_weights(x0, X1), ay = axis_weights(y0, Y1);
   const R nq = -qw;
   const int lt = m.lt;
@@ -467,7 +544,7 @@ __device__ __forceinline__ void record_pair(const Params<R> &p, const SpeciesCon
 // push also performs a sort's payload gather, kGather, which writes w too).
 template <typename R, bool kGather, typename M>
 __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const SpeciesConst<R> &K, int q,
-                                         int qi, int i, int j, Tally<R> &tl) {
+                                         int qi, int i, int j, Tally<R> &tl, bool runs = false) {
   constexpr bool kShared = std::is_same<M, SharedMesh<R>>::value;
   const Species<R> &S = K.S;
   const Species<R> &In = K.In;
@@ -525,7 +602,7 @@ __device__ __forceinline__ void push_one(const M &m, const Params<R> &p, const S
   int j1 = j + dj;
   if (j1 >= nt) { j1 = nt - 1; yn = one_minus_ulp<R>(); }
   if (!dead && m.ff(i1, j1)) dead = true;
-  if constexpr (kShared) deposit_sh<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
+  if constexpr (kShared) deposit_sh<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv, runs);
   else deposit<R>(m, K.q * w, i, j, xo, yo, X1, Y1, un[2] * ginv);
   if (dead) {
     S.cell[q] = -1;
@@ -646,11 +723,37 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
       m.s_cn[k] = (gj >= 0 && gj <= nt) ? p.t.cn[gj] : R(1);
     }
     const SpeciesConst<R> K(p, s, kGather);
-    __syncthreads();
     const int q0 = item.z, q1 = item.z + item.w;
+    // particles of one cell next to each other (co-located injected pairs
+    // keep their order through the stable sort)?  Decided once per item from
+    // blockDim.x neighbour pairs spread over it, so a scattered item pays
+    // nothing in the deposit.
+    int same = 0;
+    {
+      const int stride = max(1, (q1 - q0 - 1) / (int)blockDim.x);
+      const int qa = q0 + 1 + (int)threadIdx.x * stride;
+      if (qa < q1) {
+        const int ca = K.In.cell[kGather ? (int)K.sidx[qa] : qa];
+        const int cb = K.In.cell[kGather ? (int)K.sidx[qa - 1] : qa - 1];
+        same = (ca == cb && ca >= 0) ? 1 : 0;
+      }
+    }
+    const bool runs = __syncthreads_count(same) >= kRunItemMin;
+    // the particles this thread visits: block-strided in a scattered item;
+    // in a cell-coherent one every warp walks its own contiguous slice, so
+    // that its lanes stay consecutive (the runs) while the warps work on
+    // different cells (their atomics then rarely meet)
+    int qs = q0 + (int)threadIdx.x, qe = q1, qstep = (int)blockDim.x;
+    if (runs) {
+      const int nw = (int)blockDim.x >> 5, w = (int)threadIdx.x >> 5;
+      const int slice = ((q1 - q0 + nw - 1) / nw + 31) & ~31;
+      qs = q0 + w * slice + ((int)threadIdx.x & 31);
+      qe = min(q1, q0 + (w + 1) * slice);
+      qstep = 32;
+    }
     // a particle is handled in shared memory when its whole stencil (start
     // cell -1 .. +2 in both directions) lies inside the region
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    for (int q = qs; q < qe; q += qstep) {
       const int qi = kGather ? (int)K.sidx[q] : q;
       const int c = K.In.cell[qi];
       if (c < 0) {
@@ -660,7 +763,7 @@ __global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ P
       int i, j;
       decode_cell(p, c, i, j);
       if (i - 1 >= m.i0 && i + 2 < m.i0 + lr && j - 1 >= m.j0 && j + 2 < m.j0 + lt)
-        push_one<R, kGather>(m, p, K, q, qi, i, j, tl);
+        push_one<R, kGather>(m, p, K, q, qi, i, j, tl, runs);
       else {
         const Tally<R> t = push_one_global<R, kGather>(p, s, q, qi, i, j);
         tl.killed += t.killed; tl.radiated += t.radiated;

@@ -131,24 +131,32 @@ def test_push_deposit_parity(env, name, prec, tol):
             assert rel_l2(g[k][live], o[k][live]) < tol, k
 
 
-@pytest.mark.parametrize("cluster", [False, True])
-def test_tiled_deposit_parity(env, cluster):
+@pytest.mark.parametrize("case", ["scattered", "cluster", "cell_order"])
+def test_tiled_deposit_parity(env, case):
     """One push/deposit step of the FP32 tiled kernel (shared-memory J with
     FP32 shared atomics, flushed once per grid point) against the FP64
     oracle: J within 1e-6 in relative L2 (measured 1.2e-7 to 2.8e-7), and
     within 2e-6 with a third of the electrons, all with one momentum, piled
-    into one cell (measured up to 1.1e-6); particles as in the tail-kernel
-    test.  (An int32 fixed-point shared J, about 2^-21 of the largest
-    contribution per unit, measured 1.7e-6 to 8.7e-6 here, and 1.45e-2 with
-    a dense cell of mixed momenta.)"""
+    into one cell (measured up to 1.1e-6), which after the tile sort sit
+    next to each other, so that the deposit sums runs of equal windows
+    within the warp before its atomics; likewise with every particle in cell
+    order; particles as in the tail-kernel test.  (An int32 fixed-point
+    shared J, about 2^-21 of the largest contribution per unit, measured
+    1.7e-6 to 8.7e-6 here, and 1.45e-2 with a dense cell of mixed
+    momenta.)"""
     hff, workloads, _ = env
     cfg, sim, ref = make(env, "small_hybrid", capacity=40000, precision="fp32", sort_every=4, inject=False)
     shared_initial_state(sim, ref, seed=7)
     ps = workloads.particles(cfg, n_pairs=8000, seed=23)
-    if cluster:
+    if case == "cluster":
         e = ps[0]
         e["cell"][::3] = int(e["cell"][0])
         e["ur"][::3], e["ut"][::3], e["up"][::3] = 0.3, -0.2, 0.5
+    if case == "cell_order":
+        for s in range(2):
+            o = np.argsort(ps[s]["cell"], kind="stable")
+            ps[s] = {k: v[o] for k, v in ps[s].items()}
+    cluster = case == "cluster"
     for s in range(2):
         sim.load(s, ps[s])
         ref.set_particles(s, ps[s])
