@@ -339,8 +339,8 @@ def main():
     ap.add_argument("--order", default="scattered", choices=["scattered", "cell"],
                     help="particle order at load: as generated (scattered within each tile) or sorted by cell, "
                          "the order co-located injected pairs take in a long run")
-    ap.add_argument("--field-pass", type=int, default=None, choices=[0, 1],
-                    help="field update: 0 = one fused pass (the default), 1 = four kernels")
+    ap.add_argument("--field-pass", type=int, default=None, choices=[0, 1, 2],
+                    help="field update: 0 = chosen by grid size (the default), 1 = one fused pass, 2 = four kernels")
     ap.add_argument("--oracle-sample", default="128", choices=["128", "full"],
                     help="reference arm: time the oracle on a 128^2 sample (default) or the full workload")
     ap.add_argument("--ensemble-mode", default="graph", choices=["graph", "sequential"],
@@ -562,7 +562,7 @@ def main():
             "cells": cells,
             "sort_every": cfg["sort_every"],
             "tile": [cfg["tile_r"], cfg["tile_t"]],
-            "field_pass": int(cfg.get("field_pass", hff.FIELD_PASS_DEFAULT)),
+            "field_pass": "fused" if info0.field_pass == hff.FIELDS_FUSED else "split",
             "particle_order": args.order,
             "launch_shape": tuned or "configured",
             "l2": "inputs larger than L2 (particle state %.1f GB)" % (n_live0 * (28 if prec == "fp32" else 52) / 1e9),

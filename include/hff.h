@@ -88,8 +88,9 @@ extern "C" {
 #define HFF_DEVICE 1
 
 /* hff_config.field_pass */
-#define HFF_FIELDS_FUSED 0
-#define HFF_FIELDS_SPLIT 1
+#define HFF_FIELDS_AUTO 0
+#define HFF_FIELDS_FUSED 1
+#define HFF_FIELDS_SPLIT 2
 
 /* stage bits of hff_step_stages (a full step runs all, in this order) */
 #define HFF_ST_NODE 1      /* Psi, per-cell force-free flag; J_perp here unless
@@ -176,16 +177,21 @@ typedef struct hff_config {
                                removes it, and a smooth field changes by O(h^4)
                                per step.  0 = off (a reading: the paper is silent) */
   int32_t field_pass;       /* how the field update runs (the results agree to
-                               rounding): HFF_FIELDS_FUSED (0) = one
-                               row-pipelined pass over theta strips and row
-                               segments after the push, which computes J_perp
-                               itself and reads E and dB once (it needs a halo
-                               snapshot of E and dB, about 15% of their size
-                               on a 4096^2 grid); HFF_FIELDS_SPLIT (1) = J_perp
-                               at the nodes before the push, then four kernels
-                               after it (Faraday half step, Ampere,
-                               renormalisation and return, Faraday half step
-                               with the absorber)                               */
+                               rounding): HFF_FIELDS_FUSED = one row-pipelined
+                               pass over theta strips and row segments after
+                               the push, which computes J_perp itself and reads
+                               E and dB once (it needs a halo snapshot of E and
+                               dB, about 14% of their size on a 4096^2 grid);
+                               HFF_FIELDS_SPLIT = J_perp at the nodes before
+                               the push, then four kernels after it (Faraday
+                               half step, Ampere, renormalisation and return,
+                               Faraday half step with the absorber), each over
+                               every row at once; HFF_FIELDS_AUTO (0) = fused
+                               when segments of 32 rows give at least one wave
+                               of its blocks on a GB300 (six per SM in FP32,
+                               three in FP64, on 152 SMs), else split: on
+                               smaller grids the fused pass's row chains run
+                               on too few blocks                               */
 } hff_config;
 
 typedef struct hff_info {
@@ -200,6 +206,9 @@ typedef struct hff_info {
   int64_t pushed_tail;      /* particle pushes by the global-memory kernel       */
   int64_t readback_bytes;   /* bytes hff_get_info copies device -> host          */
   int64_t n_inst;           /* instances behind the handle (ensemble: members)   */
+  int32_t field_pass;       /* the field update this instance runs:
+                               HFF_FIELDS_FUSED or HFF_FIELDS_SPLIT (ensemble:
+                               the first member's)                              */
 } hff_info;
 
 typedef struct hff_particle_view {

@@ -138,13 +138,28 @@ int validate(const hff_config *c) {
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
   if (!(c->ff_filter >= 0.0 && c->ff_filter <= 1.0)) return fail(HFF_ERR_ARG, "ff_filter must be in [0, 1]");
-  if (c->field_pass != HFF_FIELDS_FUSED && c->field_pass != HFF_FIELDS_SPLIT)
-    return fail(HFF_ERR_ARG, "field_pass must be HFF_FIELDS_FUSED or HFF_FIELDS_SPLIT");
+  if (c->field_pass != HFF_FIELDS_AUTO && c->field_pass != HFF_FIELDS_FUSED && c->field_pass != HFF_FIELDS_SPLIT)
+    return fail(HFF_ERR_ARG, "field_pass must be HFF_FIELDS_AUTO, HFF_FIELDS_FUSED or HFF_FIELDS_SPLIT");
   if (c->inject_species[0] != c->inject_species[1])
     for (int k = 0; k < 2; ++k)
       if (c->inject_species[k] < 0 || c->inject_species[k] >= c->n_species)
         return fail(HFF_ERR_ARG, "inject_species must name existing species");
   return HFF_OK;
+}
+
+// The field update of a configuration: HFF_FIELDS_AUTO takes the fused pass
+// when segments of 32 rows give at least one wave of its blocks (six per SM
+// in FP32, three in FP64, on the 152 SMs of a GB300: a property of the grid,
+// so that hff_plan needs no GPU); on smaller grids its row chains run on too
+// few blocks and the separate passes, each over every row at once, are
+// faster (1024^2: 1.92 against 2.00 ms per step; a 32-instance ensemble of
+// grids up to 1024 x 512: 2.01 against 2.31 ms).
+static bool fused_fields(const hff_config &c) {
+  if (c.field_pass != HFF_FIELDS_AUTO) return c.field_pass == HFF_FIELDS_FUSED;
+  const bool fp64 = c.precision == HFF_FP64;
+  const int own = fuse_own_cols(fp64 ? sizeof(double) : sizeof(float));
+  const int64_t strips = (c.nt + 1 + own - 1) / own, segs = (c.nr + 1 + 31) / 32;
+  return strips * segs >= 152 * (fp64 ? 3 : 6);
 }
 
 // ----------------------------------------------------------- memory layout
@@ -260,8 +275,8 @@ void layout(const hff_config &c, Offsets &o) {
   // one wave of up to eight blocks on each of the 152 SMs of a GB300 (a
   // property of the grid, not of the device, so that hff_plan needs no GPU);
   // hff_init lengthens them to the measured occupancy
-  o.seg_rows = fuse_seg_rows(c.nr, c.nt, 152 * 8);
-  o.fsnap = c.field_pass == HFF_FIELDS_FUSED ? L.take(fuse_snap_bytes(c.nr, c.nt, o.seg_rows, R)) : 0;
+  o.seg_rows = fuse_seg_rows(c.nr, c.nt, 152 * 8, R);
+  o.fsnap = fused_fields(c) ? L.take(fuse_snap_bytes(c.nr, c.nt, o.seg_rows, R)) : 0;
   o.total = (L.off + 255) & ~size_t(255);
 }
 
@@ -276,7 +291,8 @@ struct hff_handle {
   Geom g;
   double dt = 0, psi_unit = 0, xi_abs = 0;
   int halo = 0, push_grid = 0, tail_grid = 0;
-  int seg_rows = 0;  // rows per segment of the fused field update (>= o.seg_rows)
+  bool fused = false;  // the field update runs as the fused pass (fused_fields)
+  int seg_rows = 0;    // rows per segment of the fused field update (>= o.seg_rows)
   Params<float> pf[2];
   Params<double> pd[2];
   WorkList wl{};
@@ -615,7 +631,7 @@ int enqueue_step(hff_handle *h, int par, int stages, cudaStream_t s, int parts =
   Params<R> &p = params<R>(h)[par];
   constexpr int kFieldStages = HFF_ST_FARADAY1 | HFF_ST_AMPERE | HFF_ST_CORRECT | HFF_ST_FARADAY2;
   // the fused field update computes J_perp itself from E^n, B^n
-  const bool fused = h->c.field_pass == HFF_FIELDS_FUSED && (stages & kFieldStages) == kFieldStages;
+  const bool fused = h->fused && (stages & kFieldStages) == kFieldStages;
   if ((parts & 1) && (stages & HFF_ST_NODE)) {
     launch_psi<R>(p, s);
     if (fused) launch_ffcell<R>(p, s);
@@ -1118,9 +1134,11 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
     const cudaError_t e2 = cfg->precision == HFF_FP64 ? set_field_fused_smem<double>(field_fused_smem<double>())
                                                       : set_field_fused_smem<float>(field_fused_smem<float>());
     if (e2 != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set the fused field update's shared memory size"));
+    h->fused = fused_fields(*cfg);
     // one wave of the fused field update at its occupancy on this device
     const int occ = cfg->precision == HFF_FP64 ? field_fused_blocks_per_sm<double>() : field_fused_blocks_per_sm<float>();
-    h->seg_rows = std::max(h->o.seg_rows, fuse_seg_rows(cfg->nr, cfg->nt, std::max(1, occ) * nsm));
+    h->seg_rows = std::max(h->o.seg_rows, fuse_seg_rows(cfg->nr, cfg->nt, std::max(1, occ) * nsm,
+                                                         cfg->precision == HFF_FP64 ? sizeof(double) : sizeof(float)));
   }
   if (cfg->precision == HFF_FP32) {
     fill_params<float>(h);
@@ -1452,6 +1470,7 @@ int hff_get_info(hff_handle *h, hff_info *out) {
     sum.precision = h->c.precision;
     sum.kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
     sum.kernels_launched = h->launched;
+    sum.field_pass = m0->fused ? HFF_FIELDS_FUSED : HFF_FIELDS_SPLIT;
     *out = sum;
     return HFF_OK;
   }
@@ -1473,6 +1492,7 @@ int hff_get_info(hff_handle *h, hff_info *out) {
   out->pushed_tail = (int64_t)sm.pushed[1];
   out->readback_bytes = (int64_t)sizeof(Small);
   out->n_inst = 1;
+  out->field_pass = h->fused ? HFF_FIELDS_FUSED : HFF_FIELDS_SPLIT;
   return HFF_OK;
 }
 

@@ -940,7 +940,7 @@ template <typename R> cudaError_t set_field_fused_smem(size_t bytes) { return ra
 // resident blocks (one wave: every block walks its rows once, none waits
 // for a second wave), at least 32 rows so that the warm-up stays a small
 // share
-int fuse_seg_rows(int nr, int nt, int wave_blocks) {
+int fuse_seg_rows(int nr, int nt, int wave_blocks, size_t) {
   const int strips = (nt + 1 + kFuseOwn - 1) / kFuseOwn;
   const int segs = std::max(1, wave_blocks / strips);
   return std::max(32, (nr + 1 + segs - 1) / segs);
@@ -952,6 +952,7 @@ template <typename R> int field_fused_blocks_per_sm() {
     return 0;
   return n;
 }
+int fuse_own_cols(size_t) { return kFuseOwn; }
 size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real) {
   const FuseGeom fg = fuse_geom(nr, nt, seg_rows);
   return (size_t)(fuse_snap_cols(nr, fg.strips) + fuse_snap_rows(nt, fg.segs)) * real;

@@ -249,7 +249,8 @@ template <typename R> void launch_blend_out(const Params<R> &p, R *fr, R *ft, R 
 // Ampere, renormalisation, return, Faraday half with absorber) in one pass
 // over row segments of seg_rows rows
 template <typename R> void launch_field_fused(const Params<R> &p, int seg_rows, void *snap, cudaStream_t s);
-int fuse_seg_rows(int nr, int nt, int wave_blocks);                 // rows per segment of the launch
+int fuse_own_cols(size_t real);                                     // theta columns a strip owns
+int fuse_seg_rows(int nr, int nt, int wave_blocks, size_t real);    // rows per segment of the launch
 template <typename R> int field_fused_blocks_per_sm();              // its occupancy (0 = unknown)
 size_t fuse_snap_bytes(int nr, int nt, int seg_rows, size_t real);  // its halo snapshot
 template <typename R> size_t field_fused_smem();

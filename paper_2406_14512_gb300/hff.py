@@ -30,10 +30,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhff.so")
 HFF_OK, HFF_ERR_ARG, HFF_ERR_CAPACITY, HFF_ERR_CUDA, HFF_ERR_TIMEOUT, HFF_ERR_NONFINITE = 0, -1, -2, -3, -4, -5
 GEOM = {"dipole": 0, "monopole": 1, "synth": 2, "uniform": 3, "michel": 4}
 FP32, FP64 = 0, 1
-# hff_config.field_pass: the field update as one fused pass, or split in
-# four kernels
-FIELDS_FUSED, FIELDS_SPLIT = 0, 1
-FIELD_PASS_DEFAULT = FIELDS_FUSED
+# hff_config.field_pass: the field update chosen by grid size, as one fused
+# pass, or split in four kernels
+FIELDS_AUTO, FIELDS_FUSED, FIELDS_SPLIT = 0, 1, 2
+FIELD_PASS_DEFAULT = FIELDS_AUTO
 HOST, DEVICE = 0, 1
 ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255, nocount=256)
 SCALAR_RR_SCALE = 0
@@ -72,7 +72,7 @@ class hff_info(C.Structure):
                 ("sort_every", C.c_int32), ("precision", C.c_int32),
                 ("kernels_per_step", C.c_int64), ("kernels_launched", C.c_int64),
                 ("pushed_tiled", C.c_int64), ("pushed_tail", C.c_int64),
-                ("readback_bytes", C.c_int64), ("n_inst", C.c_int64)]
+                ("readback_bytes", C.c_int64), ("n_inst", C.c_int64), ("field_pass", C.c_int32)]
 
 
 class hff_particle_view(C.Structure):

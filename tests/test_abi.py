@@ -67,7 +67,7 @@ def test_invalid_configs_are_rejected(lib, bad):
     if "precision_bad" in bad:
         c.precision = 7
     if "field_pass_bad" in bad:
-        c.field_pass = 2
+        c.field_pass = 3
     with pytest.raises(hff.HffError) as e:
         hff.hff_plan(c)
     assert e.value.code == hff.HFF_ERR_ARG

@@ -43,19 +43,22 @@ def make(env, name, **kw):
     # the corrections-only return with the fourth-difference filter of E_r, E_th
     ("small_hybrid", "fp32", 1e-5, {"ff_delta_only": 1, "ff_filter": 1.0}),
     ("small_michel", "fp64", 1e-11, {"ff_delta_only": 1, "ff_filter": 0.5}),
-    # the fused pass on two strips and several row segments (halo columns
-    # and warm-up rows crossing block boundaries), with the filter on nine
-    ("small_fine", "fp64", 1e-11, {}), ("small_fine", "fp32", 1e-5, {}),
-    ("c1", "fp64", 1e-11, {"ff_delta_only": 1, "ff_filter": 1.0}),
-    # the same steps through the four separate field kernels
+    # the fused pass (field_pass 1) on one strip and four segments, and on
+    # several strips and row segments (halo columns and warm-up rows
+    # crossing block boundaries), with the filter on nine
     ("small_hybrid", "fp32", 1e-5, {"field_pass": 1}), ("small_hybrid", "fp64", 1e-11, {"field_pass": 1}),
-    ("small_michel", "fp32", 1e-5, {"field_pass": 1}), ("small_fine", "fp64", 1e-11, {"field_pass": 1}),
-    ("small_hybrid", "fp32", 1e-5, {"field_pass": 1, "ff_delta_only": 1, "ff_filter": 1.0})])
+    ("small_michel", "fp32", 1e-5, {"field_pass": 1}),
+    ("small_fine", "fp64", 1e-11, {"field_pass": 1}), ("small_fine", "fp32", 1e-5, {"field_pass": 1}),
+    ("c1", "fp64", 1e-11, {"field_pass": 1, "ff_delta_only": 1, "ff_filter": 1.0}),
+    ("c1", "fp32", 1e-5, {"field_pass": 1, "ff_delta_only": 1, "ff_filter": 1.0}),
+    # the four separate field kernels, explicitly (the cases above without
+    # field_pass take them too: small grids)
+    ("small_fine", "fp64", 1e-11, {"field_pass": 2})])
 def test_field_step_parity(env, name, prec, tol, extra):
     """Psi, J_perp, Yee advance, blended current, renormalisation, star and
     absorber: one field-only step from identical smooth fields, through the
-    fused field pass (field_pass 0, the default) or the four separate field
-    kernels (field_pass 1)."""
+    four separate field kernels (field_pass 2, and the automatic choice on
+    these small grids) or the fused field pass (field_pass 1)."""
     cfg, sim, ref = make(env, name, capacity=0, precision=prec, sort_every=0, **extra)
     shared_initial_state(sim, ref, seed=3)
     psi_g = sim.get("psi")  # FP64 prefix of the current B_r
