@@ -353,14 +353,7 @@ void fill_params(hff_handle *h) {
     p.r_min = (R)c.r_min; p.xi_abs = (R)h->xi_abs; p.shell_r2 = (R)(c.shell_r * c.shell_r);
     p.inv_dlog = (R)(1.0 / h->g.dlog); p.inv_dth = (R)(1.0 / h->g.dth);
     p.small_grid = (h->g.dlog < 0.03 && h->g.dth < 0.03) ? 1 : 0;
-    {  // constants of the division of a cell index by nt
-      const uint64_t d = (uint64_t)c.nt;
-      int l = 0;
-      while ((1ull << l) < d) ++l;
-      p.div_m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
-      p.div_s1 = l < 1 ? l : 1;
-      p.div_s2 = l > 1 ? l - 1 : 0;
-    }
+    p.div_nt = make_fastdiv((uint32_t)c.nt);  // cell index -> row
     p.n_breaks = c.n_breaks;
     for (int k = 0; k < kMaxBreaks; ++k) {
       const double x = c.psi_break[k] * h->psi_unit;

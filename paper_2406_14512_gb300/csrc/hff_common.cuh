@@ -79,6 +79,29 @@ inline float2 psi_pair_of(double x) {
   return make_float2(h, (float)(x - (double)h));
 }
 
+// Division of an unsigned 32-bit integer by an invariant divisor d >= 1 with
+// one multiply-high, an add and two shifts (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, the
+// round-up method with an (N+1)-bit multiplier): with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n), the quotient is
+// (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+  uint32_t m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((1ull << l) < (uint64_t)d) ++l;
+  FastDiv q;
+  q.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  q.s1 = l < 1 ? l : 1;
+  q.s2 = l > 1 ? l - 1 : 0;
+  return q;
+}
+__device__ __forceinline__ uint32_t fastdiv(const FastDiv &q, uint32_t n) {
+  const uint32_t t = __umulhi(q.m, n);
+  return (t + ((n - t) >> q.s1)) >> q.s2;
+}
+
 template <typename R>
 struct Tables {
   // rows
@@ -135,7 +158,7 @@ struct Params {
   R dt, dlog, dth, omega, r_min, xi_abs, shell_r2;
   R inv_dlog, inv_dth;
   int small_grid;           // dlog and dtheta both below the series threshold
-  uint32_t div_m, div_s1, div_s2;  // cell / nt by multiplication (see decode_cell)
+  FastDiv div_nt;           // cell / nt by multiplication (see decode_cell)
   int n_breaks;
   typename PsiOf<R>::T psi_bk[kMaxBreaks];  // breakpoints, absolute units
   R f_break[kMaxBreaks];
@@ -224,8 +247,7 @@ __device__ __forceinline__ bool ff_cell(const Params<R> &p, int i, int j) {
 // l = ceil(log2 nt), s1 = min(l, 1), s2 = max(l - 1, 0)).
 template <typename R>
 __device__ __forceinline__ void decode_cell(const Params<R> &p, int c, int &i, int &j) {
-  const uint32_t n = (uint32_t)c, t = __umulhi(p.div_m, n);
-  i = (int)((t + ((n - t) >> p.div_s1)) >> p.div_s2);
+  i = (int)fastdiv(p.div_nt, (uint32_t)c);
   j = c - i * p.nt;
 }
 

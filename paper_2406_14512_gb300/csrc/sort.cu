@@ -25,11 +25,14 @@ constexpr int kSortItems = 8;
 constexpr int kSortBlock = kSortThreads * kSortItems;  // 2048 elements
 constexpr int kScanBlock = 4096;
 
-__device__ __forceinline__ uint32_t tile_key(int cell, int nt, int tile_r, int tile_t, int ntt,
-                                             int64_t ncells, uint32_t dead) {
+// the divisions by nt, tile_r and tile_t by multiplication (FastDiv): the
+// first radix pass computes the key of every slot twice (histogram and
+// scatter), and three run-time integer divisions cost several times the rest
+__device__ __forceinline__ uint32_t tile_key(int cell, int nt, const FastDiv &dnt, const FastDiv &dtr,
+                                             const FastDiv &dtt, int ntt, int64_t ncells, uint32_t dead) {
   if (cell < 0 || cell >= ncells) return dead;
-  const int i = cell / nt, j = cell - (cell / nt) * nt;
-  return (uint32_t)((i / tile_r) * ntt + j / tile_t);
+  const uint32_t i = fastdiv(dnt, (uint32_t)cell), j = (uint32_t)cell - i * (uint32_t)nt;
+  return fastdiv(dtr, i) * (uint32_t)ntt + fastdiv(dtt, j);
 }
 
 struct SortArgs {
@@ -43,12 +46,13 @@ struct SortArgs {
   unsigned *bad;            // flag word: bad_bit is or-ed in for an invalid cell
   unsigned bad_bit;
   int nb, shift, nt, tile_r, tile_t, ntt;
+  FastDiv dnt, dtr, dtt;    // divisions by nt, tile_r, tile_t
   uint32_t dead;
   bool first;
 };
 
 __device__ __forceinline__ uint32_t load_key(const SortArgs &a, int64_t e) {
-  return a.first ? tile_key(a.cell[e], a.nt, a.tile_r, a.tile_t, a.ntt, a.ncells, a.dead) : a.keys_in[e];
+  return a.first ? tile_key(a.cell[e], a.nt, a.dnt, a.dtr, a.dtt, a.ntt, a.ncells, a.dead) : a.keys_in[e];
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_hist(SortArgs a) {
@@ -338,6 +342,7 @@ void launch_sort_species(const Params<R> &p, int s, Species<R> dst, const SortSc
   a.bad_bit = kStBadCell;
   a.nb = nb;
   a.nt = p.nt; a.tile_r = p.tile_r; a.tile_t = p.tile_t; a.ntt = p.ntt;
+  a.dnt = make_fastdiv((uint32_t)p.nt); a.dtr = make_fastdiv((uint32_t)p.tile_r); a.dtt = make_fastdiv((uint32_t)p.tile_t);
   a.dead = dead;
   a.hist = ss.hist;
   uint32_t *ko = ss.keys_a, *io = ss.idx_a, *ki = ss.keys_b, *ii = ss.idx_b;
@@ -505,6 +510,7 @@ extern "C" int hff_tile_order_noalloc(const int32_t *cell, int64_t n, int32_t nr
   a.bad_bit = 1u;
   a.nb = nb;
   a.nt = nt; a.tile_r = tile_r; a.tile_t = tile_t; a.ntt = ntt;
+  a.dnt = make_fastdiv((uint32_t)nt); a.dtr = make_fastdiv((uint32_t)tile_r); a.dtt = make_fastdiv((uint32_t)tile_t);
   a.dead = dead;
   a.hist = hist;
   k_live_init<<<1, 1, 0, st>>>(live, (uint32_t)n);
