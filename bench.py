@@ -158,6 +158,37 @@ def oracle_rate(name, n_grid, steps, warm=0):
     return pst / el, el, desc, cfg
 
 
+def cpu_rate(name, n_grid, steps, procs, timeout=600):
+    """The oracle on `procs` host cores: as many independent single-threaded
+    processes, each stepping its own copy of the sample (the workload is data
+    parallel; the oracle itself stays sequential).  Rate = particle-steps of
+    all processes over the slowest one's stepping time.  The processes are
+    fresh interpreters (no CUDA state is inherited) with a time limit."""
+    if procs <= 1:
+        rate, _, desc, _ = oracle_rate(name, n_grid, steps)
+        return rate, 1, desc
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r, el, d, _ = bench.oracle_rate(%r, %d, %d); print(json.dumps([r * el, el, d]))"
+            % (ROOT, name, n_grid, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    res, t0 = [], time.perf_counter()
+    try:
+        for pr in ps:
+            out, err = pr.communicate(timeout=max(1.0, timeout - (time.perf_counter() - t0)))
+            if pr.returncode != 0:
+                raise RuntimeError(f"oracle process failed: {err.strip()[-300:]}")
+            res.append(json.loads(out.strip().splitlines()[-1]))
+    finally:
+        for pr in ps:
+            if pr.poll() is None:
+                pr.kill()
+                pr.wait()
+    work, wall = sum(r[0] for r in res), max(r[1] for r in res)
+    return work / wall, procs, f"{procs} processes, each: {res[0][2]}"
+
+
 def describe(name, cfg):
     """The workload named in `config` by both arms of the benchmark."""
     return (f"{name}: {cfg['nr']}x{cfg['nt']} log-spherical grid, r in [1, {cfg['r_max']:g}] r*, "
@@ -333,6 +364,9 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="host cores for the oracle baseline (independent single-threaded processes; 0 = all, "
+                         "at most 16)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--tile", default=None, help="tile_r x tile_t of the sort and the tiled push, e.g. 16x24")
     ap.add_argument("--sort-every", type=int, default=None)
@@ -537,8 +571,9 @@ def main():
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         try:
-            rate, cel, desc, _ = oracle_rate(args.workload, 512, 3)
-            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+            procs = args.cpu_procs if args.cpu_procs > 0 else min(16, os.cpu_count() or 1)
+            rate, cores, desc = cpu_rate(args.workload, 512, 3, procs)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
         except Exception as e:  # the oracle is test infrastructure; report, do not fail
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
     line = {

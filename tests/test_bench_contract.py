@@ -30,3 +30,16 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_multicore_oracle_baseline_runs_independent_processes():
+    """The host baseline on several cores: independent single-threaded oracle
+    processes on copies of a sample; the rate sums their particle-steps over
+    the slowest process's time, and cores counts the processes."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    rate, cores, desc = bench.cpu_rate("c1", 32, 1, 2)
+    assert cores == 2 and rate > 0 and desc.startswith("2 processes")
+    one, c1, _ = bench.cpu_rate("c1", 32, 1, 1)
+    assert c1 == 1 and one > 0
