@@ -251,8 +251,8 @@ void layout(const hff_config &c, Offsets &o) {
   const int tr = tile_r_of(c), tt = tile_t_of(c);
   o.ntt = (int)((nt + tt - 1) / tt);
   o.ntiles = (int)((nr + tr - 1) / tr) * o.ntt;
-  o.nb = (int)((cap + 2047) / 2048);
-  o.nparts = (int)(((size_t)o.nb * 256 + 4095) / 4096);
+  o.nb = (int)((cap + kSortBlock - 1) / kSortBlock);
+  o.nparts = (int)(((size_t)o.nb * 256 + kScanBlock - 1) / kScanBlock);
   o.max_items = c.n_species * (o.ntiles + (int)((cap + kChunkMin - 1) / kChunkMin)) + 1;
   if (c.sort_every > 0) {
     for (int s = 0; s < c.n_species; ++s) o.sidx[s] = L.take(cap * 4);

@@ -102,6 +102,14 @@ __device__ __forceinline__ uint32_t fastdiv(const FastDiv &q, uint32_t n) {
   return (t + ((n - t) >> q.s1)) >> q.s2;
 }
 
+// the radix sort's blocks: kSortItems rounds of kSortThreads slots each, one
+// 256-bin histogram column per block (the histogram matrix the scans pass
+// over shrinks as the blocks grow), scanned in kScanBlock pieces
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortBlock = kSortThreads * kSortItems;  // 4096 slots
+constexpr int kScanBlock = 4096;
+
 template <typename R>
 struct Tables {
   // rows

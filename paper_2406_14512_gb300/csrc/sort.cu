@@ -7,7 +7,7 @@
 // cell index outside the grid (never produced by the push; only a caller's
 // input can hold one), which is also reported through a flag word.  The sort is an
 // LSD radix sort over 8-bit digits of (key, index) pairs.  Each pass: per-block
-// digit histograms (2048 elements per block), one exclusive scan over the
+// digit histograms (kSortBlock elements per block), one exclusive scan over the
 // digit-major histogram matrix, and a stable scatter in which every element's
 // rank inside its block comes from warp match masks, so equal keys keep their
 // order (the result equals a stable sort by key).  The particle payload moves
@@ -20,10 +20,6 @@
 
 namespace hff {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortBlock = kSortThreads * kSortItems;  // 2048 elements
-constexpr int kScanBlock = 4096;
 
 // the divisions by nt, tile_r and tile_t by multiplication (FastDiv): the
 // first radix pass computes the key of every slot twice (histogram and
