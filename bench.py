@@ -314,10 +314,15 @@ def run_ensemble(args, hff, workloads, torch, ws, rank, local, dev):
         ie = ens.info()
         torch.cuda.synchronize(dev)
         te = time.perf_counter()
+        prev = None
         for k in range(ke):
             ens.set_rr_scale(1.0)
             ens.step(1)
-            last = ens.info()
+            t = ens.info_enqueue()
+            if prev is not None:
+                last = ens.info_collect(prev)
+            prev = t
+        last = ens.info_collect(prev)
         el_e2e = time.perf_counter() - te
         pst_e2e = (last.pushed_tiled + last.pushed_tail) - (ie.pushed_tiled + ie.pushed_tail)
         readback = last.readback_bytes
@@ -345,7 +350,7 @@ def run_ensemble(args, hff, workloads, torch, ws, rank, local, dev):
         "cpu_baseline": None,
         "e2e": {"value": pst_e2e_all / el_e2e, "unit": UNIT, "h2d_bytes_per_step": 8,
                 "d2h_bytes_per_step": int(readback), "steps": ke,
-                "path": "hff_set_scalar + hff_step + hff_get_info per step (Python binding, pinned staging)"},
+                "path": "hff_set_scalar + hff_step + hff_info_enqueue per step, each step's counters collected (hff_info_collect) while the next runs (Python binding, pinned staging)"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -484,13 +489,23 @@ def main():
         # ------------------------------------------------------- e2e region
         ke = args.e2e_steps or K
         ie = sim.info()
+        ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         te = time.perf_counter()
+        ee0.record(stream)
+        prev = None
         for k in range(ke):
             sim.set_rr_scale(1.0)          # per-step control scalar: pinned H2D
             sim.step(1)
-            last = sim.info()              # per-step counters: D2H, synchronises
+            t = sim.info_enqueue()         # per-step counters: D2H behind the step
+            if prev is not None:
+                last = sim.info_collect(prev)  # the previous step's, while this one runs
+            prev = t
+        ee1.record(stream)
+        last = sim.info_collect(prev)
         el_e2e = time.perf_counter() - te
+        torch.cuda.synchronize(dev)
+        e2e_device_ms = ee0.elapsed_time(ee1) / ke  # the same steps on the stream's clock
         pst_e2e = (last.pushed_tiled + last.pushed_tail) - (ie.pushed_tiled + ie.pushed_tail)
         readback = last.readback_bytes
         sim.close()
@@ -613,7 +628,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": pst_e2e_all / el_e2e, "unit": UNIT, "h2d_bytes_per_step": 8,
                 "d2h_bytes_per_step": int(readback), "steps": ke,
-                "path": "hff_set_scalar + hff_step + hff_get_info per step (Python binding, pinned staging)"},
+                "ms_per_step": 1e3 * el_e2e / ke, "device_ms_per_step": e2e_device_ms,
+                "path": "hff_set_scalar + hff_step + hff_info_enqueue per step, each step's counters collected (hff_info_collect) while the next runs (Python binding, pinned staging)"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }

@@ -320,8 +320,21 @@ int hff_particles(hff_handle *h, int inst, int species, hff_particle_view *out);
  * Synchronises the stream. */
 int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof);
 
-/* Step counter, time step, counts and the tile / precision choices. */
+/* Step counter, time step, counts and the tile / precision choices.
+ * Synchronises the stream. */
 int hff_get_info(hff_handle *h, hff_info *out);
+
+/* The same counters read back without waiting, for a caller that keeps the
+ * GPU busy: hff_info_enqueue queues a copy of the device counters on the
+ * stream behind the work queued so far (into pinned host memory owned by the
+ * handle) and returns a ticket; hff_info_collect(ticket) waits for that copy
+ * only and fills out as hff_get_info would have at the moment of the
+ * enqueue.  The last HFF_INFO_RING tickets stay collectable; an older one is
+ * HFF_ERR_ARG (overwritten), and enqueueing waits for the copy the reused
+ * slot held.  For an ensemble the ticket covers every member. */
+#define HFF_INFO_RING 8
+int hff_info_enqueue(hff_handle *h, int64_t *ticket);
+int hff_info_collect(hff_handle *h, int64_t ticket, hff_info *out);
 
 /* Read and clear the latched device status: HFF_OK, HFF_ERR_CAPACITY,
  * HFF_ERR_NONFINITE or HFF_ERR_ARG (a particle with a cell index outside the

@@ -283,6 +283,8 @@ void layout(const hff_config &c, Offsets &o) {
 }  // namespace
 
 // ------------------------------------------------------------------ handle
+constexpr int kInfoRing = HFF_INFO_RING;
+
 struct hff_handle {
   hff_config c;
   cudaStream_t st = nullptr, cap_st = nullptr;
@@ -317,7 +319,17 @@ struct hff_handle {
   // see a later value) and the counter readback
   double *pin_scalar = nullptr;
   unsigned pin_next = 0;
+  // one event per quarter of the scalar ring, recorded when the writes move
+  // on to the next quarter: a quarter is reused only after its copies ran
+  cudaEvent_t ev_scalar[4] = {};
   Small *pin_small = nullptr;
+  // asynchronous counter read-back (hff_info_enqueue / hff_info_collect): a
+  // ring of pinned copies, each with its event and the host-side counters of
+  // the moment it was queued; allocated on first use
+  Small *pin_ring = nullptr;
+  cudaEvent_t ev_info[kInfoRing] = {};
+  int64_t info_step[kInfoRing] = {}, info_launched[kInfoRing] = {};
+  int64_t info_next = 0;
   // ensemble (n_inst > 1): the members are ordinary instances carved from
   // the caller's buffer; one graph holds every member's step as a parallel
   // branch (fork streams joined by events at capture time)
@@ -976,6 +988,11 @@ void destroy_handle(hff_handle *h) {
   if (h->cap_st) cudaStreamDestroy(h->cap_st);
   if (h->pin_scalar) cudaFreeHost(h->pin_scalar);
   if (h->pin_small) cudaFreeHost(h->pin_small);
+  if (h->pin_ring) cudaFreeHost(h->pin_ring);
+  for (int k = 0; k < 4; ++k)
+    if (h->ev_scalar[k]) cudaEventDestroy(h->ev_scalar[k]);
+  for (int k = 0; k < kInfoRing; ++k)
+    if (h->ev_info[k]) cudaEventDestroy(h->ev_info[k]);
   delete h;
 }
 
@@ -1347,7 +1364,18 @@ int hff_set_scalar(hff_handle *h, int which, double value) {
     return HFF_OK;
   }
   h->c.rr_scale = value;
-  double *slot = h->pin_scalar + (h->pin_next++ % kScalarRing);
+  constexpr unsigned kQuarter = kScalarRing / 4;
+  const unsigned idx = h->pin_next++ % kScalarRing;
+  if (idx % kQuarter == 0) {
+    const unsigned q = idx / kQuarter;
+    if (!h->ev_scalar[0])
+      for (int k = 0; k < 4; ++k)
+        if (cudaEventCreateWithFlags(&h->ev_scalar[k], cudaEventDisableTiming) != cudaSuccess)
+          return fail(HFF_ERR_CUDA, "event create failed");
+    CK(cudaEventRecord(h->ev_scalar[(q + 3) % 4], h->st));  // the quarter just filled
+    CK(cudaEventSynchronize(h->ev_scalar[q]));               // the quarter about to be reused
+  }
+  double *slot = h->pin_scalar + idx;
   *slot = value;
   CK(cudaMemcpyAsync(&h->small->rr, slot, sizeof(double), cudaMemcpyHostToDevice, h->st));
   return HFF_OK;
@@ -1438,54 +1466,117 @@ int hff_diagnostics(hff_handle *h, int inst, hff_diag *out, double *l_prof) {
   return HFF_OK;
 }
 
-int hff_get_info(hff_handle *h, hff_info *out) {
-  if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
-  if (is_ensemble(h)) {  // totals over the members
-    hff_info sum;
-    std::memset(&sum, 0, sizeof(sum));
-    for (hff_handle *m : h->members) {
-      hff_info mi;
-      const int rc = hff_get_info(m, &mi);
-      if (rc != HFF_OK) return rc;
-      for (int s = 0; s < kMaxSpecies; ++s) sum.count[s] += mi.count[s];
-      sum.pushed_tiled += mi.pushed_tiled;
-      sum.pushed_tail += mi.pushed_tail;
-      sum.readback_bytes += mi.readback_bytes;
-      sum.n_inst += 1;
-    }
-    const hff_handle *m0 = h->members[0];
-    sum.dt = m0->dt;
-    sum.psi_unit = m0->psi_unit;
-    sum.step = m0->step;
-    sum.tile_r = m0->c.tile_r;
-    sum.tile_t = m0->c.tile_t;
-    sum.sort_every = h->c.sort_every;
-    sum.precision = h->c.precision;
-    sum.kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
-    sum.kernels_launched = h->launched;
-    sum.field_pass = m0->fused ? HFF_FIELDS_FUSED : HFF_FIELDS_SPLIT;
-    *out = sum;
-    return HFF_OK;
-  }
-  CK(cudaMemcpyAsync(h->pin_small, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  const Small &sm = *h->pin_small;
+// the counters of one instance from a copy of its device counters and the
+// host-side step and launch counts of the same moment
+static void fill_info(const hff_handle *h, const Small &sm, int64_t step, int64_t launched, hff_info *out) {
   std::memset(out, 0, sizeof(*out));
   out->dt = h->dt;
   out->psi_unit = h->psi_unit;
-  out->step = h->step;
+  out->step = step;
   for (int s = 0; s < kMaxSpecies; ++s) out->count[s] = sm.count[s];
   out->tile_r = h->c.tile_r;
   out->tile_t = h->c.tile_t;
   out->sort_every = h->c.sort_every;
   out->precision = h->c.precision;
   out->kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
-  out->kernels_launched = h->launched;
+  out->kernels_launched = launched;
   out->pushed_tiled = (int64_t)sm.pushed[0];
   out->pushed_tail = (int64_t)sm.pushed[1];
   out->readback_bytes = (int64_t)sizeof(Small);
   out->n_inst = 1;
   out->field_pass = h->fused ? HFF_FIELDS_FUSED : HFF_FIELDS_SPLIT;
+}
+
+// an ensemble's counters: the members' totals (counts, pushes, bytes read)
+static void ensemble_info(const hff_handle *h, const hff_info *mi, hff_info *out) {
+  hff_info sum;
+  std::memset(&sum, 0, sizeof(sum));
+  for (size_t k = 0; k < h->members.size(); ++k) {
+    for (int s = 0; s < kMaxSpecies; ++s) sum.count[s] += mi[k].count[s];
+    sum.pushed_tiled += mi[k].pushed_tiled;
+    sum.pushed_tail += mi[k].pushed_tail;
+    sum.readback_bytes += mi[k].readback_bytes;
+    sum.n_inst += 1;
+  }
+  const hff_handle *m0 = h->members[0];
+  sum.dt = m0->dt;
+  sum.psi_unit = m0->psi_unit;
+  sum.step = mi[0].step;
+  sum.tile_r = m0->c.tile_r;
+  sum.tile_t = m0->c.tile_t;
+  sum.sort_every = h->c.sort_every;
+  sum.precision = h->c.precision;
+  sum.kernels_per_step = h->k_step[0][0] ? h->k_step[0][0] : h->k_step[1][0];
+  sum.kernels_launched = h->launched;
+  sum.field_pass = m0->fused ? HFF_FIELDS_FUSED : HFF_FIELDS_SPLIT;
+  *out = sum;
+}
+
+int hff_get_info(hff_handle *h, hff_info *out) {
+  if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h)) {  // totals over the members
+    std::vector<hff_info> mi(h->members.size());
+    for (size_t k = 0; k < h->members.size(); ++k) {
+      const int rc = hff_get_info(h->members[k], &mi[k]);
+      if (rc != HFF_OK) return rc;
+    }
+    ensemble_info(h, mi.data(), out);
+    return HFF_OK;
+  }
+  CK(cudaMemcpyAsync(h->pin_small, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  fill_info(h, *h->pin_small, h->step, h->launched, out);
+  return HFF_OK;
+}
+
+int hff_info_enqueue(hff_handle *h, int64_t *ticket) {
+  if (!h || !ticket) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h)) {  // every member's copy, under one ticket
+    int64_t t = -1;
+    for (hff_handle *m : h->members) {
+      const int rc = hff_info_enqueue(m, &t);
+      if (rc != HFF_OK) return rc;
+    }
+    *ticket = t;
+    return HFF_OK;
+  }
+  if (!h->pin_ring) {
+    if (cudaMallocHost(&h->pin_ring, sizeof(Small) * kInfoRing) != cudaSuccess) {
+      h->pin_ring = nullptr;
+      return fail(HFF_ERR_CUDA, "pinned host staging failed");
+    }
+    for (int k = 0; k < kInfoRing; ++k)
+      if (cudaEventCreateWithFlags(&h->ev_info[k], cudaEventDisableTiming) != cudaSuccess)
+        return fail(HFF_ERR_CUDA, "event create failed");
+  }
+  const int64_t t = h->info_next;
+  const int slot = (int)(t % kInfoRing);
+  CK(cudaEventSynchronize(h->ev_info[slot]));  // the copy this slot held last (if any) is done
+  CK(cudaMemcpyAsync(h->pin_ring + slot, h->small, sizeof(Small), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaEventRecord(h->ev_info[slot], h->st));
+  h->info_step[slot] = h->step;
+  h->info_launched[slot] = h->launched;
+  h->info_next = t + 1;
+  *ticket = t;
+  return HFF_OK;
+}
+
+int hff_info_collect(hff_handle *h, int64_t ticket, hff_info *out) {
+  if (!h || !out) return fail(HFF_ERR_ARG, "bad arguments");
+  if (is_ensemble(h)) {
+    std::vector<hff_info> mi(h->members.size());
+    for (size_t k = 0; k < h->members.size(); ++k) {
+      const int rc = hff_info_collect(h->members[k], ticket, &mi[k]);
+      if (rc != HFF_OK) return rc;
+    }
+    ensemble_info(h, mi.data(), out);
+    return HFF_OK;
+  }
+  if (!h->pin_ring || ticket < 0 || ticket >= h->info_next || ticket < h->info_next - kInfoRing)
+    return fail(HFF_ERR_ARG, "unknown or overwritten info ticket");
+  const int slot = (int)(ticket % kInfoRing);
+  CK(cudaEventSynchronize(h->ev_info[slot]));
+  fill_info(h, h->pin_ring[slot], h->info_step[slot], h->info_launched[slot], out);
   return HFF_OK;
 }
 

@@ -37,6 +37,7 @@ FIELD_PASS_DEFAULT = FIELDS_AUTO
 HOST, DEVICE = 0, 1
 ST = dict(node=1, correct=2, push=4, faraday1=8, ampere=16, faraday2=32, inject=64, sort=128, all=255, nocount=256)
 SCALAR_RR_SCALE = 0
+INFO_RING = 8  # tickets that stay collectable (HFF_INFO_RING)
 FIELDS = ["E_r", "E_th", "E_ph", "B_r", "B_th", "B_ph", "J_r", "J_th", "J_ph", "psi",
           "jperp_r", "jperp_th", "jperp_ph", "dE_r", "dE_th", "dE_ph",
           "f_r", "f_th", "f_node", "ff_cell"]
@@ -94,7 +95,7 @@ _lib = None
 # exported symbols (checked against include/hff.h by the tests)
 SYMBOLS = ["hff_plan", "hff_init", "hff_load_particles", "hff_set_field", "hff_fields", "hff_step",
            "hff_step_timed", "hff_step_stages", "hff_set_scalar", "hff_particles", "hff_diagnostics", "hff_get_info",
-           "hff_status", "hff_destroy", "hff_last_error", "hff_tile_order_noalloc",
+           "hff_info_enqueue", "hff_info_collect", "hff_status", "hff_destroy", "hff_last_error", "hff_tile_order_noalloc",
            "hff_noalloc_last_error", "hff_species_maps", "hff_spectrum", "hff_checkpoint_size",
            "hff_checkpoint_save", "hff_checkpoint_load"]
 NOALLOC_MAX_PARTICLES = 262144
@@ -122,6 +123,8 @@ def load(path: str = LIB_PATH):
         "hff_particles": ([vp, C.c_int, C.c_int, C.POINTER(hff_particle_view)], C.c_int),
         "hff_diagnostics": ([vp, C.c_int, C.POINTER(hff_diag), vp], C.c_int),
         "hff_get_info": ([vp, C.POINTER(hff_info)], C.c_int),
+        "hff_info_enqueue": ([vp, C.POINTER(i64)], C.c_int),
+        "hff_info_collect": ([vp, i64, C.POINTER(hff_info)], C.c_int),
         "hff_status": ([vp], C.c_int),
         "hff_destroy": ([vp], C.c_int),
         "hff_last_error": ([], C.c_char_p),
@@ -264,6 +267,18 @@ def hff_diagnostics(h, inst, nr: int):
 def hff_get_info(h) -> hff_info:
     i = hff_info()
     _check(load().hff_get_info(h, C.byref(i)))
+    return i
+
+
+def hff_info_enqueue(h) -> int:
+    t = C.c_int64()
+    _check(load().hff_info_enqueue(h, C.byref(t)))
+    return t.value
+
+
+def hff_info_collect(h, ticket: int) -> hff_info:
+    i = hff_info()
+    _check(load().hff_info_collect(h, ticket, C.byref(i)))
     return i
 
 
@@ -426,6 +441,14 @@ class _Stepping:
 
     def info(self) -> hff_info:
         return hff_get_info(self.h)
+
+    def info_enqueue(self) -> int:
+        """Queue a read-back of the counters; returns a ticket for info_collect."""
+        return hff_info_enqueue(self.h)
+
+    def info_collect(self, ticket: int) -> hff_info:
+        """The counters as they were when the ticket was queued."""
+        return hff_info_collect(self.h, ticket)
 
     def status(self) -> int:
         return hff_status(self.h)

@@ -122,3 +122,10 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
         assert got[(st.__name__, "size")] == ctypes.sizeof(st), st.__name__
         for f in st._fields_:
             assert got[(st.__name__, f[0])] == getattr(st, f[0]).offset, (st.__name__, f[0])
+
+
+def test_info_ring_depth_matches_the_header():
+    import re
+    text = open(os.path.join(ROOT, "include", "hff.h")).read()
+    m = re.search(r"#define\s+HFF_INFO_RING\s+(\d+)", text)
+    assert m and int(m.group(1)) == hff.INFO_RING
