@@ -100,6 +100,7 @@ def lib():
         L.or_get_particles.argtypes = [vp, C.c_int] + [vp] * 7
         L.or_surface_count.restype = i32
         L.or_surface_count.argtypes = [vp, C.c_int]
+        L.or_set_surface_count.argtypes = [vp, C.c_int, i32]
         L.or_inject_target.restype = i32
         L.or_inject_target.argtypes = [vp, C.c_int]
         L.or_set_rr_scale.argtypes = [vp, d]
@@ -286,6 +287,11 @@ class Oracle:
 
     def surface_counts(self) -> np.ndarray:
         return np.array([self.L.or_surface_count(self.h, j) for j in range(self.nt)], np.int32)
+
+    def set_surface_counts(self, counts) -> None:
+        """Surface counts as a push elsewhere left them (the injection's input)."""
+        for j, v in enumerate(counts):
+            self.L.or_set_surface_count(self.h, j, int(v))
 
     def inject_targets(self) -> np.ndarray:
         return np.array([self.L.or_inject_target(self.h, j) for j in range(self.nt)], np.int32)

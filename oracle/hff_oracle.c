@@ -378,6 +378,7 @@ int or_get_particles(void *st, int sp, int32_t *cell, double *xo, double *yo, do
   return 0;
 }
 int32_t or_surface_count(void *st, int j) { return ((ost *)st)->surf[j]; }
+void or_set_surface_count(void *st, int j, int32_t v) { ((ost *)st)->surf[j] = v; }
 int32_t or_inject_target(void *st, int j) { return ((ost *)st)->target[j]; }
 void or_set_rr_scale(void *st, double v) { ((ost *)st)->c.rr_scale = v; }
 

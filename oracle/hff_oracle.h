@@ -129,6 +129,10 @@ int or_set_particles(void *st, int species, int64_t n, const int32_t *cell,
 int or_get_particles(void *st, int species, int32_t *cell, double *xo,
                      double *yo, double *ur, double *ut, double *up, double *w);
 int32_t or_surface_count(void *st, int j);
+/* Overwrites one surface count (particles in cell (0, j) after the last
+ * push).  For tests that hand the oracle a state pushed elsewhere and check
+ * the injection that follows from it. */
+void or_set_surface_count(void *st, int j, int32_t v);
 int32_t or_inject_target(void *st, int j);
 
 void or_set_rr_scale(void *st, double v);

@@ -71,7 +71,7 @@ def test_one_step_with_pair_creation(env, precision, tol):
         for k in ("ur", "ut", "up", "w"):
             assert rel_l2(g[k][live], o[k][live]) < 10 * tol, k
     errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
-    assert max(errs.values()) < max(tol, 2e-4 if precision == "fp32" else tol), errs
+    assert max(errs.values()) < tol, errs
     assert sim.status() == 0
 
 
@@ -92,7 +92,7 @@ def test_ten_steps_with_pair_creation_and_sorting(env, precision):
         bad, ties, err = particle_mismatches(g, o, cfg["nt"])
         assert bad == 0 and ties <= max(2, len(o["cell"]) // 2000), (s, bad, ties)
         assert err < 1e-5, err
-    tol = 2e-4 if precision == "fp32" else 1e-10
+    tol = 1e-5 if precision == "fp32" else 1e-10
     errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
     assert max(errs.values()) < tol, errs
     assert sim.status() == 0
@@ -128,5 +128,5 @@ def test_crust_extraction_with_protons(env, precision, steps):
         assert err < 1e-5, err
     tol = 1e-5 if precision == "fp32" else 1e-10
     errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
-    assert max(errs.values()) < max(tol, 2e-4 if precision == "fp32" else tol), errs
+    assert max(errs.values()) < tol, errs
     assert sim.status() == 0

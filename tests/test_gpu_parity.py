@@ -206,9 +206,9 @@ def test_gauss_law_fp32_dense_cell(env):
 def test_ten_full_steps(env, name, prec):
     """Ten whole steps (graph path: tiled push, injection, sort every 4):
     particle order and cells identical up to face ties and positions within
-    1e-5 cell.  Fields: FP64 to 1e-10; FP32 to 2e-4 in relative L2, the
-    accumulation over ten steps of FP32 rounding in the deposits (each step
-    alone is held to 1e-5 by the tests above)."""
+    1e-5 cell.  Fields: FP64 to 1e-10; FP32 to 1e-5 in relative L2 per
+    field, the single-step tolerance, after all ten steps (measured: at most
+    8e-7, E_ph of the finer grid)."""
     hff, workloads, _ = env
     cfg, sim, ref = make(env, name, capacity=60000, precision=prec, sort_every=4)
     ps = workloads.particles(cfg, n_pairs=8000, seed=31)
@@ -224,7 +224,7 @@ def test_ten_full_steps(env, name, prec):
         bad, ties, err = particle_mismatches(g, o, cfg["nt"])
         assert bad == 0 and ties <= max(2, len(o["cell"]) // 2000), (s, bad, ties)
         assert err < 1e-5, err
-    tol = 2e-4 if prec == "fp32" else 1e-10
+    tol = 1e-5 if prec == "fp32" else 1e-10
     errs = {f: rel_l2(sim.get(f), ref.get(f)) for f in FIELDS6}
     assert max(errs.values()) < tol, errs
     assert sim.status() == 0
@@ -252,7 +252,7 @@ def test_sort_bit_exact(env):
 def test_injection_bit_exact(env):
     """Top-up injection: counts, cells and offsets identical to the oracle
     (Philox4x32-10 on both sides, keyed by seed, step, cell, k)."""
-    hff, workloads, _ = env
+    hff, workloads, oracle = env
     for prec in ("fp64", "fp32"):
         cfg, sim, ref = make(env, "small_pic", capacity=50000, sort_every=0, precision=prec)
         sim.step_stages(1, ST["inject"])
@@ -265,10 +265,34 @@ def test_injection_bit_exact(env):
             assert np.array_equal(g["yo"].astype(np.float64), o["yo"])
             assert np.allclose(g["up"], o["up"], rtol=1e-6 if prec == "fp32" else 1e-14, atol=0)
             assert np.all(g["ur"] == 0) and np.all(g["ut"] == 0)
-        # later steps: the deficit follows the surface counts after each move
+        # later steps: the deficit follows the surface counts after each move.
+        # Which particles end a push in a surface cell is decided in floating
+        # point, whose rounding order differs between the two codes, so the
+        # free-running counts may differ by a particle at a cell face (loose
+        # check at the end).  The injection itself is checked exactly: the
+        # oracle injects from the GPU's own pushed state and surface counts.
         for n in range(3):
-            sim.step_stages(1, ST["node"] | ST["push"] | ST["inject"])
+            sim.step_stages(1, ST["node"] | ST["push"] | hff.ST["nocount"])
             ref.step(1, ST["node"] | ST["push"] | ST["inject"])
+            pre = [sim.particles(s) for s in range(2)]
+            chk = oracle.Oracle(cfg)
+            surf = np.zeros(cfg["nt"], np.int64)
+            for s in range(2):
+                chk.set_particles(s, pre[s])
+                c = pre[s]["cell"]
+                surf += np.bincount(c[(c >= 0) & (c < cfg["nt"])], minlength=cfg["nt"])
+            chk.set_surface_counts(surf)
+            chk.step_index = sim.info().step
+            sim.step_stages(1, ST["inject"])
+            chk.step(1, ST["inject"])
+            for s in range(2):
+                g, o = sim.particles(s), chk.particles(s)
+                assert len(g["cell"]) == len(o["cell"]) > len(pre[s]["cell"]), (n, s)
+                assert np.array_equal(g["cell"], o["cell"])
+                assert np.array_equal(g["xo"].astype(np.float64), o["xo"])
+                assert np.array_equal(g["yo"].astype(np.float64), o["yo"])
+                k = len(pre[s]["cell"])
+                assert np.allclose(g["up"][k:], o["up"][k:], rtol=1e-6 if prec == "fp32" else 1e-14, atol=0)
         for s in range(2):
             assert abs(len(sim.particles(s)["cell"]) - ref.count(s)) <= 2
 

@@ -328,6 +328,30 @@ def test_injection_restores_goldreich_julian_density(oracle_mod):
     assert o.count(0) <= n1 + nt
 
 
+def test_injection_tops_up_the_pair_deficit(oracle_mod):
+    """The top-up adds max(0, target - n/2) pairs to surface cell j, with n
+    the particles (both species) that the last push left in that cell: a
+    half-full cell receives the missing half, a full or over-full one none,
+    an empty one its whole target."""
+    cfg = pic_cfg(capacity=100000, sort_every=0)
+    o = oracle_mod.Oracle(cfg)
+    target = o.inject_targets()
+    nt = cfg["nt"]
+    assert target.max() >= 2
+    surf = np.zeros(nt, np.int64)
+    surf[0::3] = 2 * target[0::3]             # full: no pairs
+    surf[1::3] = target[1::3]                 # half full: target - target // 2 pairs
+    surf[2::3][::2] = 4 * target[2::3][::2]   # over-full: no pairs
+    o.set_surface_counts(surf)
+    o.step(1, oracle_mod.ST["inject"])
+    want = np.maximum(0, target - surf // 2)
+    assert want[1::3].sum() > 0 and want[2::3][1::2].sum() > 0
+    for s in range(2):
+        p = o.particles(s)
+        assert len(p["cell"]) == want.sum()
+        assert np.array_equal(np.bincount(p["cell"], minlength=nt)[:nt], want)
+
+
 def test_sort_is_stable_tile_order(oracle_mod):
     cfg = pic_cfg(capacity=20000, inject=False, sort_every=1, tile_r=8, tile_t=16)
     o = oracle_mod.Oracle(cfg)
