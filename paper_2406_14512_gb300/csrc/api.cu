@@ -1157,10 +1157,7 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
       const size_t smem = push_tiled_smem<float>(h->pf[0], h->halo);
       if (smem > 200 * 1024) return bail(fail(HFF_ERR_ARG, "tile + halo too large for shared memory"));
       if (set_push_smem<float>(smem) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set shared memory size"));
-      int per_sm = (int)((227 * 1024) / (smem + 1024));
-      if (per_sm < 1) per_sm = 1;
-      if (per_sm > 8) per_sm = 8;
-      h->push_grid = nsm * per_sm;
+      h->push_grid = nsm * std::max(1, std::min(8, push_tiled_blocks_per_sm<float>(smem)));
     }
   } else {
     fill_params<double>(h);
@@ -1169,10 +1166,7 @@ static int init_one(const hff_config *cfg, void *dev_mem, size_t bytes, void *st
       const size_t smem = push_tiled_smem<double>(h->pd[0], h->halo);
       if (smem > 200 * 1024) return bail(fail(HFF_ERR_ARG, "tile + halo too large for shared memory"));
       if (set_push_smem<double>(smem) != cudaSuccess) return bail(fail(HFF_ERR_CUDA, "cannot set shared memory size"));
-      int per_sm = (int)((227 * 1024) / (smem + 1024));
-      if (per_sm < 1) per_sm = 1;
-      if (per_sm > 8) per_sm = 8;
-      h->push_grid = nsm * per_sm;
+      h->push_grid = nsm * std::max(1, std::min(8, push_tiled_blocks_per_sm<double>(smem)));
     }
   }
   if (rc != HFF_OK) return bail(rc);

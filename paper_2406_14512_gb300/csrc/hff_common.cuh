@@ -303,6 +303,7 @@ template <typename R> size_t push_tiled_smem(const Params<R> &p, int halo);
 template <typename R> void launch_inject(const Params<R> &p, cudaStream_t s);
 template <typename R> void launch_step_done(const Params<R> &p, cudaStream_t s);
 template <typename R> cudaError_t set_push_smem(size_t bytes);
+template <typename R> int push_tiled_blocks_per_sm(size_t bytes);
 
 struct SortScratch {
   uint32_t *keys_a, *keys_b;   // cap

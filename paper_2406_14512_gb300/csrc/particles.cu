@@ -347,8 +347,8 @@ __device__ __forceinline__ Axis<R> axis_weights(R x0, R X1) {
 // / J_th window base and equal J_ph base) and sit next to each other form a
 // run; with at least kRunMin such neighbours in the warp, a segmented scan
 // sums each run's 16 site values and only the run's last lane issues the
-// shared atomics.  FP32 (and FP64) shared atomic adds are compare-and-swap
-// loops on this GPU, which serialise on equal addresses: particles of one
+// shared atomics.  FP32 (and FP64) shared atomic adds are retry loops of
+// about six instructions on this GPU, which serialise on equal addresses: particles of one
 // cell next to each other in memory (co-located injected pairs, or any
 // cell-coherent order) otherwise cost one retry per lane and site (a
 // cell-ordered 4096^2 workload measured 2.7x the push time of a scattered
@@ -672,8 +672,13 @@ __global__ void __launch_bounds__(256) k_push_tail(Params<R> p) {
 // ---------------------------------------------------------- tiled kernel
 // Region of a tile: cells [ti*TR - H, (ti+1)*TR + H) (and likewise in theta)
 // widened by the stencil: one node below, two above.
+// Register budget: five blocks of 256 per SM in FP32 (48 registers, a few
+// spilled values in L1; the region of a 16 x 24 tile fits five times in
+// shared memory), three in FP64, whose doubled region leaves room for no more.
+template <typename R> constexpr int push_tiled_min_blocks() { return sizeof(R) == 4 ? 5 : 3; }
 template <typename R, bool kGather>
-__global__ void __launch_bounds__(256, 4) k_push_tiled(const __grid_constant__ Params<R> p, WorkList wl, int halo) {
+__global__ void __launch_bounds__(256, push_tiled_min_blocks<R>())
+    k_push_tiled(const __grid_constant__ Params<R> p, WorkList wl, int halo) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lr = p.tile_r + 2 * halo + 4, lt = p.tile_t + 2 * halo + 4, area = lr * lt;
   R *base = reinterpret_cast<R *>(smem);
@@ -968,6 +973,15 @@ template <typename R> cudaError_t set_push_smem(size_t bytes) {
   const cudaError_t e = raise_smem_limit<push_tiled_fn<R, false>>(bytes);
   return e != cudaSuccess ? e : raise_smem_limit<push_tiled_fn<R, true>>(bytes);
 }
+// resident blocks of the tiled push per SM with `bytes` of shared memory
+// (registers and shared memory both counted); 0 on error
+template <typename R> int push_tiled_blocks_per_sm(size_t bytes) {
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_push_tiled<R, false>, 256, bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push_tiled<R, true>, 256, bytes) != cudaSuccess)
+    return 0;
+  return a < b ? a : b;
+}
 
 #define HFF_INST(R)                                                                         \
   template size_t push_tiled_smem<R>(const Params<R> &, int);                               \
@@ -975,7 +989,8 @@ template <typename R> cudaError_t set_push_smem(size_t bytes) {
   template void launch_push_tiled<R>(const Params<R> &, const WorkList &, int, cudaStream_t, int, bool); \
   template void launch_inject<R>(const Params<R> &, cudaStream_t);                          \
   template void launch_step_done<R>(const Params<R> &, cudaStream_t);                       \
-  template cudaError_t set_push_smem<R>(size_t);
+  template cudaError_t set_push_smem<R>(size_t);                                            \
+  template int push_tiled_blocks_per_sm<R>(size_t);
 HFF_INST(float)
 HFF_INST(double)
 #undef HFF_INST
