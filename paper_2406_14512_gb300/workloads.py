@@ -72,7 +72,8 @@ def config(name: str) -> dict:
     elif name == "c2":
         c = _base(1024, 1024, 60.0, 6.0, "synth", seed=1235)
         c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=25_000_000,
-                 steps=2000, precision="fp32", place="band", sheet_frac=0.2, momenta="maxwell")
+                 steps=2000, precision="fp32", place="band", sheet_frac=0.2, momenta="maxwell",
+                 tile_r=16, tile_t=24, sort_every=12)  # the autotuner's choice on this grid
     elif name == "c3":
         c = _base(4096, 4096, 100.0, 10.0, "synth", kappa=1.0, seed=1236)
         c.update(psi_break=list(TABLE1_PSI), f_break=list(TABLE1_F), n_pairs=150_000_000,
