@@ -117,6 +117,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_seed(seed, rank):
+    """Seed of rank `rank`'s replica: each rank steps an independent instance
+    of the same workload drawn from its own particles."""
+    return int(seed) + 1000 * int(rank)
+
+
 def reduce_replicas(elapsed, counts, world_size):
     """Replicas: wall time is the slowest rank's, work is the sum over ranks.
     `elapsed` and `counts` are per-rank lists of floats; returns (max, sum)."""
@@ -277,7 +283,7 @@ def run_ensemble(args, hff, workloads, torch, ws, rank, local, dev):
     import numpy as np
     cfgs = workloads.ensemble(args.workload)
     for c in cfgs:
-        c["seed"] = int(c["seed"]) + 1000 * rank
+        c["seed"] = replica_seed(c["seed"], rank)
         if args.precision:
             c["precision"] = args.precision
     if args.ensemble_mode == "sequential":
@@ -422,7 +428,7 @@ def main():
         cfg["sort_every"] = args.sort_every
     if args.field_pass is not None:
         cfg["field_pass"] = args.field_pass
-    cfg["seed"] = int(cfg["seed"]) + 1000 * rank
+    cfg["seed"] = replica_seed(cfg["seed"], rank)
     cfg["capacity"] = int(cfg["n_pairs"] * 1.1) + 100_000
     prec = cfg.get("precision", "fp32")
     t0 = time.perf_counter()
