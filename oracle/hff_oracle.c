@@ -510,13 +510,22 @@ static void correct_e(ost *s) {
   node_pass_b(s);
   /* with the literal reading the edge value moves toward the mean of the
    * corrected node fields, E <- E + f (<E''> - E); otherwise E += f <dE>;
-   * the optional filter term is subtracted with the same weight f         */
+   * the optional filter term is subtracted with the same weight f.
+   * Reading 2 returns the corrections alone except on the radial edges that
+   * end on the star (i = 0): their one interior node is node row 1, and
+   * there the corrected node field itself returns, E_r <- E_r + f (E''(1) -
+   * E_r), with E''(1) = Delta E(1) + the collocated E of row 1.  Row 0 is
+   * processed first, so that collocated E is still the uncorrected one.    */
+  int star_lit = s->c.ff_delta_only == 2;
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j <= nt; ++j) {
       double f = blend(s, 0.5 * (PSI(i, j) + PSI(i + 1, j)));
       double m = edge_r_mean(s, 13, i, j);
       if (fr) m -= fr[(int64_t)i * (nt + 1) + j];
-      if (f != 0.0) ER(i, j) += f * (lit ? m - ER(i, j) : m);
+      int star = star_lit && i == 0 && nr > 1;
+      if (star) m += 0.5 * (ER(0, j) + ER(1, j));
+      int l = lit || star;
+      if (f != 0.0) ER(i, j) += f * (l ? m - ER(i, j) : m);
     }
   for (int i = 1; i < nr; ++i)
     for (int j = 0; j < nt; ++j) {

@@ -80,7 +80,10 @@ typedef struct or_config {
   double gamma_s;            /* Lorentz factor of the created pairs          */
   int32_t inject_species[2]; /* species injected together; equal = (0, 1)   */
   int32_t ff_delta_only;     /* 0: the corrected node E returns to the edges,
-                                1: only the corrections Delta E (Sect. 3)   */
+                                1: only the corrections Delta E (Sect. 3),
+                                2: only the corrections, except on the radial
+                                edges at the star, where the corrected node
+                                E of row 1 returns                          */
   double ff_filter;          /* sigma of the fourth-difference filter of E_r
                                 along r and E_th along theta where f > 0
                                 (0 = off; 1 removes the odd-even mode)      */

@@ -7,13 +7,17 @@ by vector calculus (none of them re-types the oracle's own formulas):
   second-order convergence of B to the point dipole;
 * div B = 0 preserved by Faraday's law (Eq. 18);
 * Michel's monopole (Eqs. 32-35): force-free perpendicular current,
-  stationarity under one force-free step, the corotation boundary value,
+  stationarity under one force-free step (second order for the
+  corrections-only returns), the corotation boundary value,
   E.B = 0 and E^2 <= B^2 after the renormalisation of Eqs. 25-26, and the
   spin-down power L_M;
 * the split monopole (Michel's solution reversed in the south) away from its
   equatorial sheet: the closed-form current, and one force-free step equal
   to Michel's with the south reversed (the equations are odd in E and B);
 * the blending function of Eqs. 29-31 with the Table 1 bands;
+* the return of the corrections to the edges in closed form for uniform B,
+  with the stellar row of radial edges taking the corrected field (reading
+  2), and that reading's boundedness on the Sect. 4 set-up;
 * the absorbing layer by its purpose: an outgoing pulse passes r_abs
   undamped, decays monotonically in the layer and sends back under 1% of
   its energy (the wall alone returns most of it).
@@ -307,6 +311,8 @@ def test_michel_force_free_step_is_stationary(oracle_mod):
     then averaged 1-2-1 once per step."""
     errs, rates = michel_step_change(oracle_mod, delta_only=1)
     assert min(rates) > 1.5, (errs, rates)
+    errs, rates = michel_step_change(oracle_mod, delta_only=2)  # E_r = 0 on Michel's stellar row
+    assert min(rates) > 1.5, (errs, rates)
     errs, rates = michel_step_change(oracle_mod, delta_only=0)
     assert min(rates) > 0.9 and errs[-1] < 0.06, (errs, rates)
 
@@ -406,6 +412,68 @@ def test_corrected_field_returns_to_edges_closed_form(oracle_mod):
     o.step(1, oracle_mod.ST["correct"])
     for k in before:
         assert np.allclose(o.get(k)[3:-3, 3:-3], before[k][3:-3, 3:-3], rtol=1e-13, atol=1e-14), k
+
+
+def _renormalised(E, B):
+    """Eqs. 25-26 at one point, from their statement."""
+    ep = E - E.dot(B) / B.dot(B) * B
+    if ep.dot(ep) > B.dot(B):
+        ep = ep * math.sqrt(B.dot(B) / ep.dot(ep))
+    return ep
+
+
+@pytest.mark.parametrize("delta_only", [1, 2])
+def test_stellar_row_return_closed_form(oracle_mod, delta_only):
+    """The corrections-only return, and reading 2 which differs from it on
+    the radial edges that end on the star only.  Uniform B and E_th, E_ph;
+    E_r = a on the stellar row of radial edges and b on every other row.
+    Node row 1 collocates E_r = (a + b)/2, node row 2 collocates b; a radial
+    edge of row i >= 1 takes the mean of the two node corrections.  On the
+    stellar row reading 1 adds node 1's correction to a, reading 2 sets the
+    renormalised node-1 field itself."""
+    c = mk(12, 12, "dipole", r_max=4.0, r_lc=2.0, psi_break=[-1.0], f_break=[1.0], ff_delta_only=delta_only)
+    o = oracle_mod.Oracle(c)
+    a, b, et, ep_ = 0.7, -0.4, 1.1, 0.3
+    B = np.array([0.5, 0.2, -0.4])
+    er = np.full(o.shape("E_r"), b)
+    er[0, :] = a
+    o.set("E_r", er)
+    o.set("E_th", np.full(o.shape("E_th"), et))
+    o.set("E_ph", np.full(o.shape("E_ph"), ep_))
+    for k, v in zip(("B_r", "B_th", "B_ph"), B):
+        o.set(k, np.full(o.shape(k), v))
+    o.step(1, oracle_mod.ST["correct"])
+    e1 = np.array([0.5 * (a + b), et, ep_])
+    e2 = np.array([b, et, ep_])
+    d1, d2 = _renormalised(e1, B) - e1, _renormalised(e2, B) - e2
+    got = o.get("E_r")
+    j = 6
+    want0 = _renormalised(e1, B)[0] if delta_only == 2 else a + d1[0]
+    assert got[0, j] == pytest.approx(want0, rel=1e-13, abs=1e-14)
+    assert got[1, j] == pytest.approx(b + 0.5 * (d1[0] + d2[0]), rel=1e-13, abs=1e-14)
+    assert got[4, j] == pytest.approx(b + d2[0], rel=1e-13, abs=1e-14)
+
+
+def test_stellar_row_return_keeps_the_monopole_interface_bounded(oracle_mod):
+    """Why reading 2 exists: the Sect. 4 monopole set-up on a 24^2 mesh with
+    the northern hemisphere left in vacuum (f = 0, no particles) and the
+    southern one force-free.  With the corrections alone returning, a mode
+    that starts on the stellar rows (linearised step: a real eigenvalue of
+    1.0017, about 2 per mil growth per step) takes the fields non-finite
+    within 12,000 steps; returning the corrected field on the stellar row of
+    radial edges keeps them at Michel's scale (|E_th| <= Psi*/R_LC = 0.2 at
+    the star)."""
+    from paper_2406_14512_gb300 import monopole
+    out = {}
+    for dl in (1, 2):
+        c = monopole.config(24)
+        c.update(inject=False, capacity=0, precision="fp64", ff_delta_only=dl)
+        o = oracle_mod.Oracle(c)
+        o.step(12000)
+        out[dl] = {k: o.get(k) for k in ("E_r", "E_th", "E_ph", "B_ph")}
+    assert all(np.isfinite(v).all() for v in out[2].values())
+    assert np.abs(out[2]["E_th"]).max() < 0.21 and np.abs(out[2]["E_ph"]).max() < 0.2
+    assert not all(np.isfinite(v).all() and np.abs(v).max() < 1.0 for v in out[1].values())
 
 
 def test_failure_counters(oracle_mod):
