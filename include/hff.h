@@ -167,7 +167,14 @@ typedef struct hff_config {
                                corrections Delta E (second order on a stationary
                                solution, but it lets a mode grow near the axis
                                next to a force-free / PIC interface within
-                               ~1e4-1e5 steps on 1024^2 - 2048^2 grids)          */
+                               ~1e4-1e5 steps on 1024^2 - 2048^2 grids), 2 = the
+                               corrections, except on the radial edges that end
+                               on the star, which take the corrected field of
+                               node row 1 (their only interior node): this
+                               removes the growing mode of 1, which starts on
+                               the stellar rows.  2 runs on the separate field
+                               passes: field_pass FUSED is rejected with it, and
+                               AUTO takes the separate passes                    */
   double ff_filter;         /* sigma in [0, 1] of a fourth-difference filter of
                                E_r along r and E_th along theta, applied with the
                                correction, weighted by f: E -= f sigma/16 D4(E).

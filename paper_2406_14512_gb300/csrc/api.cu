@@ -138,6 +138,9 @@ int validate(const hff_config *c) {
     return fail(HFF_ERR_ARG, "pair creation needs gamma_th = 0 (off) or > 1, and gamma_s >= 1");
   if (c->gamma_th > 0 && c->n_species < 2) return fail(HFF_ERR_ARG, "pair creation needs species 0 and 1");
   if (!(c->ff_filter >= 0.0 && c->ff_filter <= 1.0)) return fail(HFF_ERR_ARG, "ff_filter must be in [0, 1]");
+  if (c->ff_delta_only < 0 || c->ff_delta_only > 2) return fail(HFF_ERR_ARG, "ff_delta_only must be 0, 1 or 2");
+  if (c->ff_delta_only == 2 && c->field_pass == HFF_FIELDS_FUSED)
+    return fail(HFF_ERR_ARG, "ff_delta_only = 2 runs on the separate field passes (field_pass AUTO or SPLIT)");
   if (c->field_pass != HFF_FIELDS_AUTO && c->field_pass != HFF_FIELDS_FUSED && c->field_pass != HFF_FIELDS_SPLIT)
     return fail(HFF_ERR_ARG, "field_pass must be HFF_FIELDS_AUTO, HFF_FIELDS_FUSED or HFF_FIELDS_SPLIT");
   if (c->inject_species[0] != c->inject_species[1])
@@ -156,6 +159,7 @@ int validate(const hff_config *c) {
 // grids up to 1024 x 512: 2.01 against 2.31 ms).
 static bool fused_fields(const hff_config &c) {
   if (c.field_pass != HFF_FIELDS_AUTO) return c.field_pass == HFF_FIELDS_FUSED;
+  if (c.ff_delta_only == 2) return false;  // the stellar-row return exists in the separate passes only
   const bool fp64 = c.precision == HFF_FP64;
   const int own = fuse_own_cols(fp64 ? sizeof(double) : sizeof(float));
   const int64_t strips = (c.nt + 1 + own - 1) / own, segs = (c.nr + 1 + 31) / 32;
@@ -431,6 +435,7 @@ void fill_params(hff_handle *h) {
     p.inj_sp[0] = dflt ? 0 : c.inject_species[0];
     p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
     p.ff_interp_e = c.ff_delta_only ? 0 : 1;
+    p.ff_star_lit = c.ff_delta_only == 2 ? 1 : 0;
     p.ff_sigma16 = (R)(c.ff_filter / 16.0);
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;
@@ -1667,7 +1672,7 @@ static bool same_run(const hff_config &a, const hff_config &b) {
             a.seed == b.seed && a.tile_r == b.tile_r && a.tile_t == b.tile_t && a.sort_every == b.sort_every &&
             a.precision == b.precision && a.gamma_th == b.gamma_th && a.gamma_s == b.gamma_s &&
             a.inject_species[0] == b.inject_species[0] && a.inject_species[1] == b.inject_species[1] &&
-            (a.ff_delta_only != 0) == (b.ff_delta_only != 0) && a.ff_filter == b.ff_filter;
+            a.ff_delta_only == b.ff_delta_only && a.ff_filter == b.ff_filter;
   for (int k = 0; k < 4; ++k)
     eq = eq && a.psi_break[k] == b.psi_break[k] && a.f_break[k] == b.f_break[k] && a.q[k] == b.q[k] && a.m[k] == b.m[k];
   return eq;

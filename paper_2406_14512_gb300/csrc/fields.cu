@@ -332,6 +332,9 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
   if (i >= 1 && i < nr) {
     R e[3], b[3];
     collocate(p, i, j, e, b);
+    // the stellar-row return needs row 1's collocated E_r before any edge
+    // moves: kept in the (zero) J_PIC slot of the radial edge (0, j)
+    if (i == 1 && p.ff_star_lit) p.f.jr[ix(0, j, n1)] = e[0];
     const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
     if (b2 > b2min<R>()) {
       const R s = (e[0] * b[0] + e[1] * b[1] + e[2] * b[2]) / b2;
@@ -356,7 +359,9 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
 
 // Delta E interpolated back to the staggered mesh by arithmetic means and
 // applied with the blend weight f (Sect. 3, Eqs. 29-31); or, with
-// ff_interp_e, the corrected node field itself: E <- E + f (<E''> - E).
+// ff_interp_e, the corrected node field itself: E <- E + f (<E''> - E); with
+// ff_star_lit, Delta E everywhere except the radial edges at the star, which
+// take E''(1) (their only interior node).
 // The optional filter term (node pass B, in the J_PIC arrays) is subtracted
 // with the same weight and its slot cleared for the next deposit.
 template <typename R>
@@ -370,11 +375,15 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   if (i < nr) {
     const int64_t k = ix(i, j, n1);
     const R fb = blend_redge(p, i, j);
-    R g = R(0);
-    if (filt) { g = f.jr[k]; f.jr[k] = R(0); }
+    // ff_star_lit: the radial edge at the star (one interior node, row 1)
+    // takes the corrected node field E''(1) = Delta E(1) + collocated E(1)
+    const bool star = p.ff_star_lit && i == 0 && nr > 1;
+    R g = R(0), e1 = R(0);
+    if (star) { e1 = f.jr[k]; f.jr[k] = R(0); }
+    else if (filt) { g = f.jr[k]; f.jr[k] = R(0); }
     if (fb != R(0)) {
-      const R m = edge_r_mean(f.der, i, j, nr, n1) - g;
-      f.er[k] += fb * (lit ? m - f.er[k] : m);
+      const R m = edge_r_mean(f.der, i, j, nr, n1) - g + e1;
+      f.er[k] += fb * ((lit || star) ? m - f.er[k] : m);
     }
   }
   if (i >= 1 && i < nr) {

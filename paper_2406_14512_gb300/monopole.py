@@ -104,7 +104,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=2000)
     ap.add_argument("--layer", type=float, default=0.0, help="transition layer width in Psi* (0 = sharp cut)")
     ap.add_argument("--ff-delta-only", type=int, default=0,
-                    help="1: only the corrections Delta E return to the edges, 0: the corrected E (Sect. 3)")
+                    help="0: the corrected E returns to the edges (Sect. 3); 1: only the corrections "
+                         "Delta E; 2: the corrections, the corrected E on the radial edges at the star")
     ap.add_argument("--ppc", type=float, default=4.0, help="largest injected pairs per surface cell")
     ap.add_argument("--ff-filter", type=float, default=0.0,
                     help="sigma of the fourth-difference filter of E_r, E_th (0 = off)")

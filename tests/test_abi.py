@@ -48,7 +48,8 @@ def test_plan_sizes_scale_with_grid_and_capacity(lib):
 
 @pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=33), dict(n_breaks_bad=True),
                                  dict(r_abs="one_cell_inside"), dict(precision_bad=True),
-                                 dict(field_pass_bad=True)])
+                                 dict(field_pass_bad=True), dict(ff_delta_only=3),
+                                 dict(ff_delta_only=2, field_pass=1)])
 def test_invalid_configs_are_rejected(lib, bad):
     cfg = workloads.config("small_pic")
     cfg.update(capacity=10)
@@ -68,6 +69,9 @@ def test_invalid_configs_are_rejected(lib, bad):
         c.precision = 7
     if "field_pass_bad" in bad:
         c.field_pass = 3
+    if "ff_delta_only" in bad:  # 2 (the stellar-row return) exists in the separate passes only
+        c.ff_delta_only = bad["ff_delta_only"]
+        c.field_pass = bad.get("field_pass", 0)
     with pytest.raises(hff.HffError) as e:
         hff.hff_plan(c)
     assert e.value.code == hff.HFF_ERR_ARG

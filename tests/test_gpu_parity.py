@@ -43,6 +43,10 @@ def make(env, name, **kw):
     # the corrections-only return with the fourth-difference filter of E_r, E_th
     ("small_hybrid", "fp32", 1e-5, {"ff_delta_only": 1, "ff_filter": 1.0}),
     ("small_michel", "fp64", 1e-11, {"ff_delta_only": 1, "ff_filter": 0.5}),
+    # the corrections-only return with the corrected field on the stellar row
+    # (ff_delta_only 2), alone and with the filter sharing the J_PIC slots
+    ("small_hybrid", "fp32", 1e-5, {"ff_delta_only": 2}), ("small_michel", "fp64", 1e-11, {"ff_delta_only": 2}),
+    ("small_hybrid", "fp64", 1e-11, {"ff_delta_only": 2, "ff_filter": 1.0}),
     # the fused pass (field_pass 1) on one strip and four segments, and on
     # several strips and row segments (halo columns and warm-up rows
     # crossing block boundaries), with the filter on nine
