@@ -205,16 +205,18 @@ def test_gauss_law_fp32_dense_cell(env):
     assert sim.status() == 0
 
 
-@pytest.mark.parametrize("name,prec", [("small_pic", "fp64"), ("small_hybrid", "fp32"), ("small_rr", "fp32"),
-                                       ("small_fine", "fp32")])
-def test_ten_full_steps(env, name, prec):
+@pytest.mark.parametrize("name,prec,extra", [
+    ("small_pic", "fp64", {}), ("small_hybrid", "fp32", {}), ("small_rr", "fp32", {}), ("small_fine", "fp32", {}),
+    # reading 2 of the field return (the stellar row takes the corrected field)
+    ("small_hybrid", "fp64", {"ff_delta_only": 2}), ("small_hybrid", "fp32", {"ff_delta_only": 2})])
+def test_ten_full_steps(env, name, prec, extra):
     """Ten whole steps (graph path: tiled push, injection, sort every 4):
     particle order and cells identical up to face ties and positions within
     1e-5 cell.  Fields: FP64 to 1e-10; FP32 to 1e-5 in relative L2 per
     field, the single-step tolerance, after all ten steps (measured: at most
     8e-7, E_ph of the finer grid)."""
     hff, workloads, _ = env
-    cfg, sim, ref = make(env, name, capacity=60000, precision=prec, sort_every=4)
+    cfg, sim, ref = make(env, name, capacity=60000, precision=prec, sort_every=4, **extra)
     ps = workloads.particles(cfg, n_pairs=8000, seed=31)
     for s in range(2):
         sim.load(s, ps[s])
