@@ -461,8 +461,9 @@ def test_stellar_row_return_keeps_the_monopole_interface_bounded(oracle_mod):
     that starts on the stellar rows (linearised step: a real eigenvalue of
     1.0017, about 2 per mil growth per step) takes the fields non-finite
     within 12,000 steps; returning the corrected field on the stellar row of
-    radial edges keeps them at Michel's scale (|E_th| <= Psi*/R_LC = 0.2 at
-    the star)."""
+    radial edges keeps them finite and E at Michel's scale (|E_th| <=
+    Psi*/R_LC = 0.2 at the star; B_ph, not asserted, still grows to several
+    times Michel's value on this coarse mesh)."""
     from paper_2406_14512_gb300 import monopole
     out = {}
     for dl in (1, 2):
