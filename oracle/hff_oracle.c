@@ -20,7 +20,9 @@
  *   4. Ampere      : E^n -> E^{n+1} with J = (1-f) J_PIC + f J_FFE (Eqs. 19, 28)
  *                    then the corotating star (Sect. 4) and the absorber
  *   5. correction  : node pass B renormalises the collocated E^{n+1} against
- *                    B^{n+1/2} (Eqs. 25-26); E += f <Delta E> on the mesh
+ *                    B^{n+1/2} (Eqs. 25-26); the mesh E moves to f <E''>
+ *                    (default reading), or takes E += f <Delta E> (readings 1
+ *                    and 2; reading 2 returns E'' on the stellar radial edges)
  *   6. Faraday     : B^{n+1/2} -> B^{n+1} from the corrected E, absorber on B
  *   7. injection   : top-up of the surface pair density (Sects. 4, 5.1),
  *                    then the pairs of the threshold pair creation (Sect. 5.1)
