@@ -15,6 +15,8 @@ by vector calculus (none of them re-types the oracle's own formulas):
   equatorial sheet: the closed-form current, and one force-free step equal
   to Michel's with the south reversed (the equations are odd in E and B);
 * the blending function of Eqs. 29-31 with the Table 1 bands;
+* one correction stage in the field-energy norm (non-expansive for the
+  literal return, not for the corrections-only one);
 * the return of the corrections to the edges in closed form for uniform B,
   with the stellar row of radial edges taking the corrected field (reading
   2), and that reading's boundedness on the Sect. 4 set-up;
@@ -456,25 +458,41 @@ def test_stellar_row_return_closed_form(oracle_mod, delta_only):
 
 def test_stellar_row_return_keeps_the_monopole_interface_bounded(oracle_mod):
     """Why reading 2 exists: the Sect. 4 monopole set-up on a 24^2 mesh with
-    the northern hemisphere left in vacuum (f = 0, no particles) and the
-    southern one force-free.  With the corrections alone returning, a mode
-    that starts on the stellar rows (linearised step: a real eigenvalue of
-    1.0017, about 2 per mil growth per step) takes the fields non-finite
-    within 12,000 steps; returning the corrected field on the stellar row of
-    radial edges keeps them finite and E at Michel's scale (|E_th| <=
-    Psi*/R_LC = 0.2 at the star; B_ph, not asserted, still grows to several
-    times Michel's value on this coarse mesh)."""
+    the northern hemisphere left in vacuum (f = 0, no particles), the
+    southern one force-free and the absorber 4 cells deep.  With the
+    corrections alone returning, the fields leave Michel's solution and
+    reach several times its scale within 12,000 steps; returning the
+    corrected field on the stellar row of radial edges keeps E_th, E_ph and
+    B_ph at Michel's scale (|E_th| and |B_ph| at most Psi*/R_LC = 0.2 at the
+    star)."""
     from paper_2406_14512_gb300 import monopole
     out = {}
     for dl in (1, 2):
         c = monopole.config(24)
-        c.update(inject=False, capacity=0, precision="fp64", ff_delta_only=dl)
+        dlog = math.log(c["r_max"] / c["r_min"]) / c["nr"]
+        c.update(inject=False, capacity=0, precision="fp64", ff_delta_only=dl,
+                 r_abs=c["r_max"] * math.exp(-4 * dlog))
         o = oracle_mod.Oracle(c)
         o.step(12000)
         out[dl] = {k: o.get(k) for k in ("E_r", "E_th", "E_ph", "B_ph")}
     assert all(np.isfinite(v).all() for v in out[2].values())
-    assert np.abs(out[2]["E_th"]).max() < 0.21 and np.abs(out[2]["E_ph"]).max() < 0.2
+    assert np.abs(out[2]["E_th"]).max() < 0.21 and np.abs(out[2]["E_ph"]).max() < 0.15
+    assert np.abs(out[2]["B_ph"]).max() < 0.25
     assert not all(np.isfinite(v).all() and np.abs(v).max() < 1.0 for v in out[1].values())
+
+
+def test_correction_stage_in_the_field_energy_norm(oracle_mod):
+    """One correction stage around Michel's monopole (force-free everywhere,
+    12^2), measured in the norm in which the Yee pair conserves vacuum
+    energy: the literal return (1-2-1 means of the corrected field) cannot
+    raise the energy of a perturbation in the interior or along the axis
+    (largest singular value <= 1); the corrections-only returns can (> 1):
+    the arithmetic-mean return is not the adjoint of the collocation under
+    the log-r, sin(theta) volumes."""
+    from oracle.field_return_analysis import stage
+    lit, corr = stage(12, 0), stage(12, 1)
+    assert lit["interior"] <= 1.0 + 1e-9 and lit["axis band"] <= 1.0 + 1e-9, lit
+    assert corr["interior"] > 1.01 and corr["axis band"] > 1.01, corr
 
 
 def test_failure_counters(oracle_mod):
