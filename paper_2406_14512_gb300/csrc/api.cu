@@ -434,8 +434,9 @@ void fill_params(hff_handle *h) {
     const bool dflt = c.inject_species[0] == c.inject_species[1];
     p.inj_sp[0] = dflt ? 0 : c.inject_species[0];
     p.inj_sp[1] = dflt ? 1 : c.inject_species[1];
-    p.ff_interp_e = c.ff_delta_only ? 0 : 1;
-    p.ff_star_lit = c.ff_delta_only == 2 ? 1 : 0;
+    // 1: the corrected node E returns (ff_delta_only 0); 0: Delta E (1);
+    // 2: Delta E, the radial edges at the star taking E''(1) (2)
+    p.ff_interp_e = c.ff_delta_only == 0 ? 1 : (c.ff_delta_only == 2 ? 2 : 0);
     p.ff_sigma16 = (R)(c.ff_filter / 16.0);
     p.w_inj = (R)c.w_inj;
     p.acc = h->small->acc;

@@ -304,7 +304,8 @@ __global__ void __launch_bounds__(kRowThreads) k_ampere(Params<R> p) {
 // Renormalisation at interior nodes from E^{n+1} and B^{n+1/2}:
 // E' = E - (E.B) B/B^2 (Eq. 25), E'' = sqrt(B^2/E'^2) E' if E'^2 > B^2 (Eq. 26).
 // Stores Delta E = E'' - E, or E'' itself when the corrected field returns to
-// the edges (ff_interp_e).  With the optional fourth-difference filter it also
+// the edges (ff_interp_e = 1; 0 and 2 return the corrections, see
+// k_correct).  With the optional fourth-difference filter it also
 // stores sigma/16 D4 E_r (along r) at the E_r edge (i+1/2, j) and sigma/16
 // D4 E_th (along theta) at the E_th edge (i, j+1/2), from the same
 // uncorrected E, in the J_PIC arrays: those are zero between Ampere's law and
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
     collocate(p, i, j, e, b);
     // the stellar-row return needs row 1's collocated E_r before any edge
     // moves: kept in the (zero) J_PIC slot of the radial edge (0, j)
-    if (i == 1 && p.ff_star_lit) p.f.jr[ix(0, j, n1)] = e[0];
+    if (i == 1 && p.ff_interp_e == 2) p.f.jr[ix(0, j, n1)] = e[0];
     const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
     if (b2 > b2min<R>()) {
       const R s = (e[0] * b[0] + e[1] * b[1] + e[2] * b[2]) / b2;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
       d2 = sc * z - e[2];
       clamped = e2 > b2;
     }
-    if (p.ff_interp_e) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
+    if (p.ff_interp_e == 1) { d0 += e[0]; d1 += e[1]; d2 += e[2]; }
   }
   // running count of Eq. 26 activations (failure detection: a force-free
   // region that keeps needing the clamp is going unstable)
@@ -359,9 +360,9 @@ __global__ void __launch_bounds__(kRowThreads) k_node_b(Params<R> p) {
 
 // Delta E interpolated back to the staggered mesh by arithmetic means and
 // applied with the blend weight f (Sect. 3, Eqs. 29-31); or, with
-// ff_interp_e, the corrected node field itself: E <- E + f (<E''> - E); with
-// ff_star_lit, Delta E everywhere except the radial edges at the star, which
-// take E''(1) (their only interior node).
+// ff_interp_e = 1, the corrected node field itself: E <- E + f (<E''> - E);
+// with ff_interp_e = 2, Delta E everywhere except the radial edges at the
+// star, which take E''(1) (their only interior node).
 // The optional filter term (node pass B, in the J_PIC arrays) is subtracted
 // with the same weight and its slot cleared for the next deposit.
 template <typename R>
@@ -370,14 +371,14 @@ __global__ void __launch_bounds__(kRowThreads) k_correct(Params<R> p) {
   const int nr = p.nr, nt = p.nt, n1 = nt + 1;
   if (j > nt) return;
   const Fields<R> &f = p.f;
-  const bool lit = p.ff_interp_e != 0;
+  const bool lit = p.ff_interp_e == 1;
   const bool filt = p.ff_sigma16 != R(0);
   if (i < nr) {
     const int64_t k = ix(i, j, n1);
     const R fb = blend_redge(p, i, j);
-    // ff_star_lit: the radial edge at the star (one interior node, row 1)
+    // ff_interp_e = 2: the radial edge at the star (one interior node, row 1)
     // takes the corrected node field E''(1) = Delta E(1) + collocated E(1)
-    const bool star = p.ff_star_lit && i == 0 && nr > 1;
+    const bool star = p.ff_interp_e == 2 && i == 0 && nr > 1;
     R g = R(0), e1 = R(0);
     if (star) { e1 = f.jr[k]; f.jr[k] = R(0); }
     else if (filt) { g = f.jr[k]; f.jr[k] = R(0); }
@@ -692,7 +693,7 @@ __global__ void __launch_bounds__(kFuseThreads) k_field_fused(Params<R> p, R hdt
   const R sh0 = jh ? t.sh[j] : R(0), shm = (j >= 1 && j <= nt) ? t.sh[j - 1] : R(0);
   const R idch = jn ? t.inv_dch[j] : R(0);
   const R dt = p.dt, fp4 = R(4.0 * kPi) * p.dt;
-  const bool lit = p.ff_interp_e != 0, filt = p.ff_sigma16 != R(0);
+  const bool lit = p.ff_interp_e == 1, filt = p.ff_sigma16 != R(0);
   const bool axis = (j == 0 || j == nt);
   unsigned long long nclamp = 0;
   // blend weights of rows k-1, k-2, k-3 (E_r edge, E_th edge, node)

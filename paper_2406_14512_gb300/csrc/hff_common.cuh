@@ -194,7 +194,6 @@ struct Params {
   int inject;
   int n_inj, inj_sp[2];     // species created together by the injection
   int ff_interp_e;          // 1: the corrected node E returns to the edges, 0: only Delta E
-  int ff_star_lit;          // with ff_interp_e = 0: the radial edges at the star take the corrected E of row 1
   R ff_sigma16;             // fourth-difference filter of E_r (r) and E_th (theta): sigma / 16
   R w_inj;
   double *acc;              // [4] injected, killed, radiated, nonfinite
