@@ -43,3 +43,20 @@ def test_multicore_oracle_baseline_runs_independent_processes():
     assert cores == 2 and rate > 0 and desc.startswith("2 processes")
     one, c1, _ = bench.cpu_rate("c1", 32, 1, 1)
     assert c1 == 1 and one > 0
+
+
+def test_push_traffic_record_matches_the_push_sources():
+    """roofline.traffic of the benchmark line comes from the committed ncu
+    record of the tiled push, and only while the push's sources are the ones
+    it was taken on (their SHA-256): an edit to them without a new capture
+    turns the field into null.  Checked here so that such an edit shows."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "profiles", "push_tiled_traffic.json")) as f:
+        rec = json.load(f)
+    n = 299_833_365
+    t = bench.push_traffic(rec["workload"], n)
+    assert t is not None, "push sources changed since profiles/push_tiled_traffic.json was captured"
+    assert t == rec["dram_bytes_per_particle"] * n
+    assert 52.0 <= rec["dram_bytes_per_particle"] < 60.0     # algorithmic 52 B, a few re-reads
+    assert bench.push_traffic("another workload", n) is None
