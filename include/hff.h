@@ -405,10 +405,9 @@ int hff_checkpoint_load(hff_handle *h, int inst, const void *src, size_t bytes);
  * Scratch lives in one fixed device array per GPU (about 4.3 MB), reserved in
  * every process that loads the library until it exits; nothing is allocated.
  * The first call on a device looks up that array's device address, so make
- * it before any stream capture.  Every call synchronises `stream` to read the
- * live count back, so no call can be made while the stream is being
- * captured.  Calls share the array: calls that overlap on the GPU (other
- * streams, threads) race and must be serialised by the caller.
+ * it before any stream capture.  Calls share the array: calls that overlap
+ * on the GPU (other streams, threads) race and must be serialised by the
+ * caller.
  * Returns HFF_ERR_CAPACITY if n > HFF_NOALLOC_MAX_PARTICLES, HFF_ERR_ARG for
  * invalid arguments or a cell index at or past nr * nt (such a particle is
  * ordered with the removed ones), HFF_ERR_CUDA if a CUDA call fails; the
