@@ -117,9 +117,16 @@ def stage(n: int, reading: int) -> dict:
 
 
 def step(n: int, reading: int, pre: int, top: int = 6, r_abs: float = 0.0) -> list:
-    """Eigenvalues of largest modulus of one whole field step, with the three
-    largest entries of each eigenvector (field name and index)."""
-    o = Oracle(sect4_config(n, reading, r_abs=r_abs))
+    """Eigenvalues of largest modulus of one whole field step of the Sect. 4
+    set-up, with the three largest entries of each eigenvector (field name
+    and index)."""
+    return spectrum(sect4_config(n, reading, r_abs=r_abs), pre, top)
+
+
+def spectrum(cfg: dict, pre: int, top: int = 6) -> list:
+    """Eigenvalues of largest modulus of one whole step of the oracle
+    configured by `cfg` (no particles), linearised `pre` steps in."""
+    o = Oracle(cfg)
     o.step(pre)
     shapes = [o.shape(k) for k in ALL_NAMES]
     sizes = [int(np.prod(s)) for s in shapes]

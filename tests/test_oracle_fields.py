@@ -5,7 +5,9 @@ by vector calculus (none of them re-types the oracle's own formulas):
   theta-prefix of Eq. 27 at every node;
 * the face-averaged B of an exactly known field (uniform B_z) and the
   second-order convergence of B to the point dipole;
-* div B = 0 preserved by Faraday's law (Eq. 18);
+* div B = 0 preserved by Faraday's law (Eq. 18), and no growing mode of the
+  vacuum step (its linearisation's eigenvalues stay on or inside the unit
+  circle);
 * Michel's monopole (Eqs. 32-35): force-free perpendicular current,
   stationarity under one force-free step (second order for the
   corrections-only returns), the corotation boundary value,
@@ -479,6 +481,20 @@ def test_stellar_row_return_keeps_the_monopole_interface_bounded(oracle_mod):
     assert np.abs(out[2]["E_th"]).max() < 0.21 and np.abs(out[2]["E_ph"]).max() < 0.15
     assert np.abs(out[2]["B_ph"]).max() < 0.25
     assert not all(np.isfinite(v).all() and np.abs(v).max() < 1.0 for v in out[1].values())
+
+
+@pytest.mark.parametrize("geom", ["monopole", "dipole"])
+def test_vacuum_step_has_no_growing_mode(oracle_mod, geom):
+    """The Yee step of Eqs. 18-19 in vacuum, at half the Courant limit, with
+    the corotating star and the absorber, linearised on a 12^2 mesh: no
+    eigenvalue lies outside the unit circle (static fields give |lambda| =
+    1).  A wrong sign in one circulation of Faraday's law puts eigenvalues
+    near 2.2 here."""
+    from oracle.field_return_analysis import sect4_config, spectrum
+    c = sect4_config(12, 0, geom=geom)
+    c.update(psi_break=[100.0], f_break=[0.0])  # f = 0 everywhere, no particles
+    top = spectrum(c, 50, top=4)
+    assert max(m for m, _, _ in top) < 1.0 + 1e-6, top
 
 
 def test_correction_stage_in_the_field_energy_norm(oracle_mod):
