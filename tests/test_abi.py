@@ -46,6 +46,18 @@ def test_plan_sizes_scale_with_grid_and_capacity(lib):
     assert 15e9 < b3 < 40e9, b3
 
 
+def test_stellar_row_return_takes_the_separate_field_passes(lib):
+    """ff_delta_only = 2 exists in the separate field kernels only: on a grid
+    where the automatic choice is the fused pass (4096^2), the plan then
+    reserves no halo snapshot for it, and the fused pass's own explicit
+    request plans the snapshot."""
+    c = dict(workloads.config("c3"), capacity=1000, tile_r=16, tile_t=24, sort_every=12)
+    fused = hff.hff_plan(hff.config_struct(c))
+    split = hff.hff_plan(hff.config_struct(dict(c, field_pass=2)))
+    auto2 = hff.hff_plan(hff.config_struct(dict(c, ff_delta_only=2)))
+    assert fused > split and auto2 == split, (fused, split, auto2)
+
+
 @pytest.mark.parametrize("bad", [dict(nr=4), dict(courant=1.5), dict(sort_every=33), dict(n_breaks_bad=True),
                                  dict(r_abs="one_cell_inside"), dict(precision_bad=True),
                                  dict(field_pass_bad=True), dict(ff_delta_only=3),
