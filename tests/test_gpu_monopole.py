@@ -9,7 +9,9 @@ step (the stable reading of Sect. 3's "interpolate these back"), measures
 6.9% at 512^2, 3.7% at 1024^2, 2.0% at 2048^2 and 1.36% at 4096^2: first-order
 convergence, from the per-step averaging of that return.  The second-order
 return of the corrections alone grows a mode next to the force-free / PIC
-interface.  What is checked: the run stays finite and clean, eps falls with
+interface; returning the corrected field on the stellar row of radial edges
+as well (ff_delta_only = 2) keeps the run finite but lets the force-free
+solution drift away from Michel's at 1024^2 and 2048^2.  What is checked: the run stays finite and clean, eps falls with
 resolution at no worse than first order and stays within 15% of the values
 measured above (a regression in either direction fails), the spin-down near
 the star is within 3% of Michel's L_M = 2 Psi*^2 Omega^2 / 3c at 1024^2, and
