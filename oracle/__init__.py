@@ -1,8 +1,9 @@
 """ctypes wrapper of the plain FP64 CPU oracle (``hff_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` are the only callers.  The product path never
-imports this package.  Configuration arrives as a plain dict (the workload
+CPU-baseline leg of ``bench.py`` are the only callers, besides this package's
+own stability analysis of the field return (``field_return_analysis``, run by
+hand and by the tests).  The product path never imports this package.  Configuration arrives as a plain dict (the workload
 description of ``paper_2406_14512_gb300.workloads``); nothing here is shared
 with the CUDA library.
 """
