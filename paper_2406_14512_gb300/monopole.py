@@ -85,7 +85,8 @@ def run(n: int = 1024, periods: float = 2.0, chunk: int = 2000, log=None, layer:
     wall = time.perf_counter() - t0
     d, prof = sim.diagnostics()
     lm = michel(cfg)["L_M"]
-    out = {"n": n, "periods": periods, "layer": layer, "ff_delta_only": cfg.get("ff_delta_only", 0),
+    out = {"n": n, "periods": periods, "layer": layer, "precision": cfg["precision"],
+           "ff_delta_only": cfg.get("ff_delta_only", 0),
            "ff_filter": cfg.get("ff_filter", 0.0),
            "ppc": cfg["ppc"],
            "steps": steps, "dt": dt, "wall_s": wall,
@@ -109,8 +110,10 @@ def main():
     ap.add_argument("--ppc", type=float, default=4.0, help="largest injected pairs per surface cell")
     ap.add_argument("--ff-filter", type=float, default=0.0,
                     help="sigma of the fourth-difference filter of E_r, E_th (0 = off)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="fields and particles in FP32 (production) or FP64")
     a = ap.parse_args()
-    kw = {"ff_delta_only": a.ff_delta_only, "ppc": a.ppc, "ff_filter": a.ff_filter}
+    kw = {"ff_delta_only": a.ff_delta_only, "ppc": a.ppc, "ff_filter": a.ff_filter, "precision": a.precision}
     print(json.dumps(run(a.n, a.periods, a.chunk, log=lambda m: print(m, file=sys.stderr, flush=True),
                          layer=a.layer, **kw)))
 
